@@ -1,0 +1,149 @@
+/*
+ * tf.h -- C ABI of the GB300 BTTB/BCCB sensitivity-product library (libtf.so).
+ *
+ * The library applies the sensitivity matrix G of potential-field inversion and its
+ * transpose to vectors and blocks of vectors (Renaut, Hogue & Vatankhah, "Fast
+ * focusing inversion of gravity and magnetic data...", arXiv:2004.13904):
+ *
+ *   G = [G^(1), ..., G^(nz)]                           (Sec. 2.1, Eq. (3))
+ *   each G^(r) is BTTB; it is embedded in a BCCB matrix whose first column, reshaped to
+ *   T_r of size (sx+nx-1) x (sy+ny-1), has the precomputed 2-D FFT  G^_r  (App. A);
+ *   G x   = sum_r extract(ifft2(G^_r .* fft2(pad(x^(r)))))   (App. A)
+ *   G^T y = [extract(ifft2(conj(G^_r) .* fft2(pad(y))))]_r    (App. A, last paragraph)
+ *   G~ x  = W_d (G (W^-1 x))                                  (Sec. 2.5, Eq. (10))
+ *
+ * Geometry (Sec. 2.1, Fig. 1): cells are indexed 0<=p<nx, 0<=q<ny, 0<=r<nz with
+ * nx = sx+pxl+pxr, ny = sy+pyl+pyr; cell p spans [p dx, (p+1) dx]; station (i,j) sits at
+ * height station_z over the centre of cell (i+pxl, j+pyl); layer r spans
+ * [z_edges[r], z_edges[r+1]] with z positive down.  m = sx*sy, n = nx*ny*nz.
+ * Vectors: model x has index p + nx*(q + ny*r); data d has index i + sx*j.
+ * Blocks are column-major: column b of X starts at X + b*ldx.
+ *
+ * Conventions for every call:
+ *  - every function returns a tf_status; tf_last_error() gives a message for the
+ *    last failure on the calling thread (library-owned string).  Nothing throws.
+ *  - vectors and blocks are DEVICE pointers owned by the caller, of the operator's
+ *    dtype (float for TF_F32, double for TF_F64), on the device that was current when
+ *    the operator was created; that device must be current for every call.
+ *  - products are asynchronous and ordered on the caller's stream (a cudaStream_t
+ *    passed as tf_stream; NULL = legacy default stream).  Inputs must not alias outputs.
+ *  - the operator owns its spectra and a workspace; calls on one operator must be
+ *    ordered (one stream, or caller-side synchronisation).  Different operators are
+ *    independent.
+ *  - colscale (length n) and rowscale (length m) are optional diagonal scalings;
+ *    NULL means identity.
+ */
+#ifndef TF_H
+#define TF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TF_OK = 0,
+  TF_EINVAL = 1,        /* invalid argument (null pointer, bad size, bad geometry)   */
+  TF_ENOMEM = 2,        /* device allocation failed                                  */
+  TF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed               */
+  TF_EUNSUPPORTED = 4,  /* valid but outside what this build supports (FFT size)     */
+  TF_ENOTCONV = 5,      /* reserved for iterative drivers                            */
+  TF_ETIMEOUT = 6       /* reserved for bounded device-side waits                    */
+} tf_status;
+
+typedef enum { TF_F32 = 0, TF_F64 = 1 } tf_dtype;
+
+typedef void* tf_stream; /* a cudaStream_t */
+
+/* Station/volume geometry (Sec. 2.1, Fig. 1; padding counts per side, Sec. 3.2). */
+typedef struct {
+  int sx, sy;                 /* stations along x and y (>= 1)                         */
+  int nz;                     /* depth layers (>= 1)                                    */
+  int pxl, pxr, pyl, pyr;     /* padding cells per side (>= 0), no stations over them   */
+  double dx, dy;              /* cell sizes in metres (> 0)                             */
+  const double* z_edges;      /* HOST array of nz+1 strictly increasing depths (m)      */
+  double station_z;          /* station depth (m), <= z_edges[0]                        */
+} tf_grid;
+
+typedef struct tf_op tf_op;
+
+/* Build the layer spectra G^_r of the vertical-attraction kernel (Sec. 2.1, Eq. (3);
+ * App. A "the 2DFFT of T is precomputed").  Units: mGal per g/cc.  The kernel table and
+ * its 2-D FFT are evaluated on the device in FP64; for TF_F32 the spectra are then
+ * rounded once to FP32.  Blocks the calling thread until the set-up is complete.
+ * Errors: TF_EINVAL (null pointers, sizes < 1, negative padding, non-increasing
+ * z_edges, station below the top of the volume), TF_EUNSUPPORTED (embedding larger
+ * than 1024 along x or y), TF_ENOMEM, TF_ECUDA.  On error *out is set to NULL. */
+tf_status tf_create_gravity(const tf_grid* grid, tf_dtype dtype, tf_stream stream, tf_op** out);
+
+/* Same for the total-field anomaly of induced magnetisation without remanence or
+ * self-demagnetisation (Sec. 2.1): inclination/declination in degrees of the inducing
+ * field (x north, y east, z down) and its strength in nT.  Units: nT per SI. */
+tf_status tf_create_magnetic(const tf_grid* grid, double inc_deg, double dec_deg,
+                             double field_nt, tf_dtype dtype, tf_stream stream, tf_op** out);
+
+/* Release the operator and everything it owns (waits for its work to finish).
+ * NULL is accepted. */
+tf_status tf_destroy(tf_op* op);
+
+/* m = sx*sy, n = nx*ny*nz. */
+tf_status tf_dims(const tf_op* op, int64_t* m, int64_t* n);
+
+/* FFT sizes chosen for the embedding: n1 >= sx+nx-1, n2 >= sy+ny-1 (any such size gives
+ * the exact product, because T is zero beyond the minimum size). */
+tf_status tf_fft_dims(const tf_op* op, int* n1, int* n2);
+
+/* d = diag(rowscale) G diag(colscale) x   (Sec. 2.5 Eq. (10); App. A)
+ * x: n values, d: m values.  Errors: TF_EINVAL (null x/d or op), TF_ECUDA. */
+tf_status tf_matvec(tf_op* op, const void* x, void* d, const void* colscale,
+                    const void* rowscale, tf_stream stream);
+
+/* x = diag(colscale) G^T diag(rowscale) y   (App. A, last paragraph)
+ * y: m values, x: n values. */
+tf_status tf_rmatvec(tf_op* op, const void* y, void* x, const void* colscale,
+                     const void* rowscale, tf_stream stream);
+
+/* D = diag(rowscale) G diag(colscale) X for B columns (Sec. 2.5: block products are
+ * loops over columns; here the spectra are shared by the whole block).
+ * X: column b at X + b*ldx (ldx >= n); D: column b at D + b*ldd (ldd >= m).
+ * B = 0 is a no-op.  Errors: TF_EINVAL (B < 0, ldx < n, ldd < m, null pointers). */
+tf_status tf_matmat(tf_op* op, int64_t B, const void* X, int64_t ldx, void* D, int64_t ldd,
+                    const void* colscale, const void* rowscale, tf_stream stream);
+
+/* X = diag(colscale) G^T diag(rowscale) Y for B columns; Y: ldy >= m, X: ldx >= n.
+ * (X^T G^T = (G X)^T and Y^T G = (G^T Y)^T need no further entry, App. A.) */
+tf_status tf_rmatmat(tf_op* op, int64_t B, const void* Y, int64_t ldy, void* X, int64_t ldx,
+                     const void* colscale, const void* rowscale, tf_stream stream);
+
+/* Copy the operator's layer spectra, nz x n2 x (n1/2+1) complex values of its dtype
+ * (interleaved re/im, k1 fastest), already divided by n1*n2, to dst (device or host
+ * memory; bytes must equal that size).  Ordered on stream.  For checks and tools. */
+tf_status tf_get_spectra(const tf_op* op, void* dst, int64_t bytes, tf_stream stream);
+
+/* Tuning knobs of the product kernels: rows-stage sequence pairs per CTA (4, 8, 16),
+ * column-stage k1 columns per CTA (4, 8, 16), and columns per workspace chunk (>= 1;
+ * the workspace is reallocated to fit).  0 keeps the current value.  Must not be
+ * called while products of this operator are in flight. */
+tf_status tf_set_tuning(tf_op* op, int rows_tile, int cols_tile, int64_t chunk_cols);
+tf_status tf_get_tuning(const tf_op* op, int* rows_tile, int* cols_tile, int64_t* chunk_cols);
+
+/* Per-stage timing with CUDA events recorded around every stage launch on the call's
+ * stream.  Enable (1) / disable (0) clears the record.  tf_profile_read synchronises
+ * on the recorded events and returns, for the stages
+ *   0 rows_r2c (model rows), 1 cols_fwd, 2 rows_c2r (data rows),
+ *   3 rows_r2c (data rows),  4 cols_adj, 5 rows_c2r (model rows),
+ * the total milliseconds, the number of launches and the columns processed
+ * (arrays of length 6). */
+tf_status tf_profile_enable(tf_op* op, int enable);
+tf_status tf_profile_read(tf_op* op, double* ms, int64_t* launches, int64_t* columns);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* tf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TF_H */

@@ -1,0 +1,210 @@
+"""GB300-native BTTB/BCCB sensitivity products for fast focusing inversion.
+
+``Operator`` wraps one tf_op of libtf.so (include/tf.h): the layer spectra of a gravity
+or magnetic sensitivity matrix G, and the products G X, G^T Y on CUDA tensors.  PyTorch
+provides device memory and streams only; every step of a product runs in the
+library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import TFError, TF_F32, TF_F64  # noqa: F401
+
+__all__ = ["Operator", "TFError", "STAGES"]
+
+STAGES = ("rows_r2c_model", "cols_fwd", "rows_c2r_data",
+          "rows_r2c_data", "cols_adj", "rows_c2r_model")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Operator:
+    """G for one station/volume geometry (Sec. 2.1), applied by 2-D FFTs (App. A).
+
+    grid: object with sx, sy, nz, pxl, pxr, pyl, pyr, dx, dy, z_edges, station_z.
+    kind: "gravity" (mGal per g/cc) or "magnetic" (nT per SI, needs inc/dec in degrees).
+    dtype: torch.float32 (FP32 spectra and FFTs) or torch.float64 (plain FP64 path).
+    """
+
+    def __init__(self, grid, kind: str = "gravity", inc: float = 90.0, dec: float = 0.0,
+                 field_nt: float = 50000.0, dtype=None, device=None):
+        torch = _torch()
+        self.dtype = torch.float32 if dtype is None else dtype
+        if self.dtype not in (torch.float32, torch.float64):
+            raise ValueError("dtype must be torch.float32 or torch.float64")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        L = _lib.lib()
+        gs, self._z = _lib.make_grid(grid)
+        dt = TF_F32 if self.dtype == torch.float32 else TF_F64
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            if kind == "gravity":
+                _lib.check(L.tf_create_gravity(ctypes.byref(gs), dt, stream, ctypes.byref(h)))
+            elif kind == "magnetic":
+                _lib.check(L.tf_create_magnetic(ctypes.byref(gs), float(inc), float(dec),
+                                                float(field_nt), dt, stream, ctypes.byref(h)))
+            else:
+                raise ValueError(f"unknown kind {kind!r}")
+        self._h = h
+        self.kind = kind
+        m = ctypes.c_int64()
+        n = ctypes.c_int64()
+        _lib.check(L.tf_dims(h, ctypes.byref(m), ctypes.byref(n)))
+        self.m, self.n = m.value, n.value
+        n1 = ctypes.c_int()
+        n2 = ctypes.c_int()
+        _lib.check(L.tf_fft_dims(h, ctypes.byref(n1), ctypes.byref(n2)))
+        self.n1, self.n2 = n1.value, n2.value
+        self.nz = int(grid.nz)
+
+    # -- plumbing -----------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().tf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        torch = _torch()
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _vec(self, t, length, name):
+        torch = _torch()
+        if t is None:
+            return None
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != self.dtype:
+            raise TypeError(f"{name} must be a {self.dtype} tensor on {self.device}")
+        if t.numel() != length or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with {length} elements")
+        return t
+
+    @staticmethod
+    def _ptr(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+    def _block(self, t, rows, name):
+        """(B, rows) tensor whose row b is column b of a column-major block."""
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != self.dtype:
+            raise TypeError(f"{name} must be a {self.dtype} tensor on {self.device}")
+        if t.dim() == 1:
+            t = t.view(1, -1)
+        if t.dim() != 2 or t.shape[1] != rows or t.stride(1) != 1 or (
+                t.shape[0] > 1 and t.stride(0) < rows):
+            raise ValueError(f"{name} must have shape (B, {rows}) with unit inner stride")
+        return t, (t.stride(0) if t.shape[0] > 1 else rows)
+
+    # -- products -----------------------------------------------------------------------
+    def matmat(self, X, colscale=None, rowscale=None, out=None):
+        """D = diag(rowscale) G diag(colscale) X; X is (B, n), result (B, m)."""
+        torch = _torch()
+        X, ldx = self._block(X, self.n, "X")
+        B = X.shape[0]
+        if out is None:
+            out = torch.empty((B, self.m), device=self.device, dtype=self.dtype)
+        D, ldd = self._block(out, self.m, "out")
+        cs = self._vec(colscale, self.n, "colscale")
+        rs = self._vec(rowscale, self.m, "rowscale")
+        _lib.check(_lib.lib().tf_matmat(self._h, B, self._ptr(X), ldx, self._ptr(D), ldd,
+                                        self._ptr(cs), self._ptr(rs), self._stream()))
+        return out
+
+    def rmatmat(self, Y, colscale=None, rowscale=None, out=None):
+        """X = diag(colscale) G^T diag(rowscale) Y; Y is (B, m), result (B, n)."""
+        torch = _torch()
+        Y, ldy = self._block(Y, self.m, "Y")
+        B = Y.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n), device=self.device, dtype=self.dtype)
+        X, ldx = self._block(out, self.n, "out")
+        cs = self._vec(colscale, self.n, "colscale")
+        rs = self._vec(rowscale, self.m, "rowscale")
+        _lib.check(_lib.lib().tf_rmatmat(self._h, B, self._ptr(Y), ldy, self._ptr(X), ldx,
+                                         self._ptr(cs), self._ptr(rs), self._stream()))
+        return out
+
+    def matvec(self, x, colscale=None, rowscale=None, out=None):
+        torch = _torch()
+        x = self._vec(x, self.n, "x")
+        if out is None:
+            out = torch.empty(self.m, device=self.device, dtype=self.dtype)
+        d = self._vec(out, self.m, "out")
+        cs = self._vec(colscale, self.n, "colscale")
+        rs = self._vec(rowscale, self.m, "rowscale")
+        _lib.check(_lib.lib().tf_matvec(self._h, self._ptr(x), self._ptr(d), self._ptr(cs),
+                                        self._ptr(rs), self._stream()))
+        return out
+
+    def rmatvec(self, y, colscale=None, rowscale=None, out=None):
+        torch = _torch()
+        y = self._vec(y, self.m, "y")
+        if out is None:
+            out = torch.empty(self.n, device=self.device, dtype=self.dtype)
+        x = self._vec(out, self.n, "out")
+        cs = self._vec(colscale, self.n, "colscale")
+        rs = self._vec(rowscale, self.m, "rowscale")
+        _lib.check(_lib.lib().tf_rmatvec(self._h, self._ptr(y), self._ptr(x), self._ptr(cs),
+                                         self._ptr(rs), self._stream()))
+        return out
+
+    # -- host-buffer convenience (copies in and out on the current stream) --------------
+    def matmat_host(self, X_host, out_host=None):
+        """G X for a pinned host block: H2D copy, product, D2H copy, all stream-ordered."""
+        torch = _torch()
+        Xd = X_host.to(self.device, non_blocking=True)
+        Dd = self.matmat(Xd)
+        if out_host is None:
+            out_host = torch.empty(Dd.shape, dtype=self.dtype, pin_memory=True)
+        out_host.copy_(Dd, non_blocking=True)
+        return out_host
+
+    def rmatmat_host(self, Y_host, out_host=None):
+        torch = _torch()
+        Yd = Y_host.to(self.device, non_blocking=True)
+        Xd = self.rmatmat(Yd)
+        if out_host is None:
+            out_host = torch.empty(Xd.shape, dtype=self.dtype, pin_memory=True)
+        out_host.copy_(Xd, non_blocking=True)
+        return out_host
+
+    # -- introspection ------------------------------------------------------------------
+    def spectra(self):
+        """Layer spectra (nz, n2, n1//2+1) complex, divided by n1*n2 (set-up output)."""
+        torch = _torch()
+        nh = self.n1 // 2 + 1
+        cdt = torch.complex64 if self.dtype == torch.float32 else torch.complex128
+        out = torch.empty((self.nz, self.n2, nh), dtype=cdt, device=self.device)
+        nbytes = out.numel() * out.element_size()
+        _lib.check(_lib.lib().tf_get_spectra(self._h, self._ptr(out), nbytes, self._stream()))
+        return out
+
+    def set_tuning(self, rows_tile=0, cols_tile=0, chunk_cols=0):
+        _lib.check(_lib.lib().tf_set_tuning(self._h, rows_tile, cols_tile, chunk_cols))
+
+    def tuning(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _lib.check(_lib.lib().tf_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def profile(self, enable: bool):
+        _lib.check(_lib.lib().tf_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 6)()
+        la = (ctypes.c_int64 * 6)()
+        co = (ctypes.c_int64 * 6)()
+        _lib.check(_lib.lib().tf_profile_read(self._h, ms, la, co))
+        return {STAGES[i]: (ms[i], la[i], co[i]) for i in range(6)}

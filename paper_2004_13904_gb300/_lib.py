@@ -1,0 +1,91 @@
+"""ctypes binding of libtf.so: the C ABI declared in include/tf.h, same names.
+
+This module only marshals arguments.  Every product runs in the library's CUDA
+kernels; if the library is missing or cannot be loaded, ``lib()`` raises -- there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtf.so")
+
+TF_OK, TF_EINVAL, TF_ENOMEM, TF_ECUDA, TF_EUNSUPPORTED, TF_ENOTCONV, TF_ETIMEOUT = range(7)
+TF_F32, TF_F64 = 0, 1
+STATUS_NAMES = {0: "TF_OK", 1: "TF_EINVAL", 2: "TF_ENOMEM", 3: "TF_ECUDA",
+                4: "TF_EUNSUPPORTED", 5: "TF_ENOTCONV", 6: "TF_ETIMEOUT"}
+
+
+class tf_grid(ctypes.Structure):
+    _fields_ = [("sx", ctypes.c_int), ("sy", ctypes.c_int), ("nz", ctypes.c_int),
+                ("pxl", ctypes.c_int), ("pxr", ctypes.c_int), ("pyl", ctypes.c_int),
+                ("pyr", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("z_edges", ctypes.POINTER(ctypes.c_double)), ("station_z", ctypes.c_double)]
+
+
+class TFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+vp = ctypes.c_void_p
+i64 = ctypes.c_int64
+c_int = ctypes.c_int
+P = ctypes.POINTER
+
+SIGNATURES = {
+    "tf_create_gravity": [P(tf_grid), c_int, vp, P(vp)],
+    "tf_create_magnetic": [P(tf_grid), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                           c_int, vp, P(vp)],
+    "tf_destroy": [vp],
+    "tf_dims": [vp, P(i64), P(i64)],
+    "tf_fft_dims": [vp, P(c_int), P(c_int)],
+    "tf_matvec": [vp, vp, vp, vp, vp, vp],
+    "tf_rmatvec": [vp, vp, vp, vp, vp, vp],
+    "tf_matmat": [vp, i64, vp, i64, vp, i64, vp, vp, vp],
+    "tf_rmatmat": [vp, i64, vp, i64, vp, i64, vp, vp, vp],
+    "tf_get_spectra": [vp, vp, i64, vp],
+    "tf_set_tuning": [vp, c_int, c_int, i64],
+    "tf_get_tuning": [vp, P(c_int), P(c_int), P(i64)],
+    "tf_profile_enable": [vp, c_int],
+    "tf_profile_read": [vp, P(ctypes.c_double), P(i64), P(i64)],
+}
+
+
+def lib():
+    """Load libtf.so (built in-tree by ``paper_2004_13904_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2004_13904_gb300.build` (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, args in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = c_int
+    L.tf_last_error.argtypes = []
+    L.tf_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(status: int) -> None:
+    if status != TF_OK:
+        raise TFError(status, lib().tf_last_error().decode(errors="replace"))
+
+
+def make_grid(g):
+    """tf_grid from any object with sx, sy, nz, pxl, pxr, pyl, pyr, dx, dy, z_edges,
+    station_z attributes; returns (struct, keepalive array)."""
+    z = (ctypes.c_double * (g.nz + 1))(*[float(v) for v in g.z_edges])
+    s = tf_grid(int(g.sx), int(g.sy), int(g.nz), int(g.pxl), int(g.pxr), int(g.pyl),
+                int(g.pyr), float(g.dx), float(g.dy), ctypes.cast(z, P(ctypes.c_double)),
+                float(g.station_z))
+    return s, z

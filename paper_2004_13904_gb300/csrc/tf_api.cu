@@ -1,0 +1,542 @@
+// C ABI of libtf.so: operator set-up (layer spectra), products, tuning and profiling.
+// Declarations and argument contracts are in include/tf.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <cstdarg>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tf.h"
+#include "tf_internal.h"
+
+using tfk::CT;
+using tfk::FftPlan;
+
+namespace {
+
+thread_local std::string g_err;
+
+tf_status fail(tf_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+tf_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? TF_ENOMEM : TF_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+constexpr int kMaxFft = 1024;
+constexpr int kStages = 6;
+
+// radices of one length-n transform; false if n has a prime factor above 7
+bool factor(int n, std::vector<int>& rad) {
+  rad.clear();
+  int m = n;
+  while (m % 8 == 0) { rad.push_back(8); m /= 8; }
+  if (m % 4 == 0) { rad.push_back(4); m /= 4; }
+  if (m % 2 == 0) { rad.push_back(2); m /= 2; }
+  for (int p : {7, 5, 3})
+    while (m % p == 0) { rad.push_back(p); m /= p; }
+  return m == 1 && (int)rad.size() <= tfk::kMaxPass;
+}
+
+// Smallest-cost transform length >= nmin: cost ~ n * (passes + 1), since every pass
+// moves all n values through shared memory once and the stage loads/stores once more.
+int choose_length(int nmin) {
+  int best = -1;
+  double best_cost = 1e300;
+  std::vector<int> rad;
+  for (int n = nmin; n <= 2 * nmin + 16; ++n) {
+    if (!factor(n, rad)) continue;
+    const double cost = (double)n * (rad.size() + 1);
+    if (cost < best_cost) { best_cost = cost; best = n; }
+  }
+  return best;
+}
+
+struct HostPlan {
+  FftPlan plan;
+  std::vector<double> tw;  // interleaved re, im
+};
+
+HostPlan make_plan(int n) {
+  HostPlan h;
+  std::vector<int> rad;
+  factor(n, rad);
+  std::memset(&h.plan, 0, sizeof h.plan);
+  h.plan.n = n;
+  h.plan.np = (int)rad.size();
+  int ns = 1, off = 0;
+  for (int p = 0; p < h.plan.np; ++p) {
+    const int R = rad[p];
+    h.plan.radix[p] = R;
+    h.plan.ns[p] = ns;
+    h.plan.tw_off[p] = off;
+    const long double L = (long double)ns * R;
+    for (int k = 0; k < ns; ++k)
+      for (int r = 1; r < R; ++r) {
+        // w^(r k) with w = exp(-2 pi i / (ns R)); r*k < ns*R, so no reduction is needed
+        const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (r * k) / L;
+        h.tw.push_back((double)cosl(ang));
+        h.tw.push_back((double)sinl(ang));
+      }
+    off += ns * (R - 1);
+    ns *= R;
+  }
+  h.plan.tw_count = off;
+  return h;
+}
+
+}  // namespace
+
+struct tf_op {
+  // geometry
+  int sx, sy, nz, nx, ny, pxl, pxr, pyl, pyr;
+  double dx, dy, station_z;
+  std::vector<double> z_edges;
+  int kind;  // 0 gravity, 1 magnetic
+  double inc, dec, field;
+  tf_dtype dtype;
+  int device;
+  // transforms
+  int n1, n2, nh;
+  HostPlan p1, p2;
+  void* tw1 = nullptr;  // device twiddles in the op dtype
+  void* tw2 = nullptr;
+  void* spec = nullptr; // [nz][n2][nh] complex of the op dtype
+  // workspace
+  void* w1 = nullptr;   // chunk * nz*ny*nh complex
+  void* w2 = nullptr;   // chunk * sy*nh complex
+  int64_t chunk = 0;
+  int rows_tile = 8, cols_tile = 8;
+  // profiling
+  bool prof = false;
+  struct Rec { int stage; int64_t cols; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+
+  size_t csize() const { return dtype == TF_F32 ? sizeof(float2) : sizeof(double2); }
+  int64_t m() const { return (int64_t)sx * sy; }
+  int64_t n() const { return (int64_t)nx * ny * nz; }
+  int64_t w1_per_col() const { return (int64_t)nz * ny * nh; }
+  int64_t w2_per_col() const { return (int64_t)sy * nh; }
+};
+
+namespace {
+
+void free_op(tf_op* op) {
+  if (!op) return;
+  cudaFree(op->tw1);
+  cudaFree(op->tw2);
+  cudaFree(op->spec);
+  cudaFree(op->w1);
+  cudaFree(op->w2);
+  for (auto& r : op->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : op->pool) cudaEventDestroy(e);
+  delete op;
+}
+
+tf_status upload_twiddles(const HostPlan& h, tf_dtype dt, void** dst) {
+  const size_t count = h.tw.size() / 2;
+  const size_t bytes = std::max<size_t>(1, count) * (dt == TF_F32 ? sizeof(float2) : sizeof(double2));
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(twiddles)");
+  if (count == 0) return TF_OK;
+  if (dt == TF_F64) {
+    e = cudaMemcpy(*dst, h.tw.data(), count * sizeof(double2), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> f(h.tw.size());
+    for (size_t i = 0; i < f.size(); ++i) f[i] = (float)h.tw[i];
+    e = cudaMemcpy(*dst, f.data(), count * sizeof(float2), cudaMemcpyHostToDevice);
+  }
+  return e == cudaSuccess ? TF_OK : cuda_fail(e, "cudaMemcpy(twiddles)");
+}
+
+tf_status alloc_workspace(tf_op* op, int64_t chunk) {
+  cudaFree(op->w1);
+  cudaFree(op->w2);
+  op->w1 = op->w2 = nullptr;
+  op->chunk = 0;
+  cudaError_t e = cudaMalloc(&op->w1, (size_t)chunk * op->w1_per_col() * op->csize());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+  e = cudaMalloc(&op->w2, (size_t)chunk * op->w2_per_col() * op->csize());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+  op->chunk = chunk;
+  return TF_OK;
+}
+
+// Default chunk: keep the per-chunk intermediate (the row-transformed model block) near
+// 48 MB so that it stays resident in the 126 MB L2 between the row and column stages.
+int64_t default_chunk(const tf_op* op) {
+  const double per = (double)op->w1_per_col() * op->csize();
+  int64_t c = (int64_t)(48.0e6 / per);
+  if (c < 1) c = 1;
+  if (c > 4096) c = 4096;
+  return c;
+}
+
+tf_status create_common(const tf_grid* g, int kind, double inc, double dec, double field,
+                        tf_dtype dt, tf_stream stream, tf_op** out) {
+  if (!out) return fail(TF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!g) return fail(TF_EINVAL, "grid is NULL");
+  if (dt != TF_F32 && dt != TF_F64) return fail(TF_EINVAL, "unknown dtype %d", (int)dt);
+  if (g->sx < 1 || g->sy < 1 || g->nz < 1)
+    return fail(TF_EINVAL, "sx, sy, nz must be >= 1 (got %d, %d, %d)", g->sx, g->sy, g->nz);
+  if (g->pxl < 0 || g->pxr < 0 || g->pyl < 0 || g->pyr < 0)
+    return fail(TF_EINVAL, "padding counts must be >= 0");
+  if (!(g->dx > 0) || !(g->dy > 0)) return fail(TF_EINVAL, "dx, dy must be > 0");
+  if (!g->z_edges) return fail(TF_EINVAL, "z_edges is NULL");
+  for (int r = 0; r < g->nz; ++r)
+    if (!(g->z_edges[r + 1] > g->z_edges[r]))
+      return fail(TF_EINVAL, "z_edges must be strictly increasing (index %d)", r);
+  if (!(g->z_edges[0] >= g->station_z))
+    return fail(TF_EINVAL, "stations must lie at or above the top of the volume");
+  if (kind == 1 && !(field > 0)) return fail(TF_EINVAL, "field strength must be > 0");
+
+  tf_op* op = new tf_op();
+  op->sx = g->sx; op->sy = g->sy; op->nz = g->nz;
+  op->pxl = g->pxl; op->pxr = g->pxr; op->pyl = g->pyl; op->pyr = g->pyr;
+  op->nx = g->sx + g->pxl + g->pxr;
+  op->ny = g->sy + g->pyl + g->pyr;
+  op->dx = g->dx; op->dy = g->dy; op->station_z = g->station_z;
+  op->z_edges.assign(g->z_edges, g->z_edges + g->nz + 1);
+  op->kind = kind; op->inc = inc; op->dec = dec; op->field = field;
+  op->dtype = dt;
+  cudaGetDevice(&op->device);
+
+  const int n1min = op->sx + op->nx - 1, n2min = op->sy + op->ny - 1;
+  op->n1 = choose_length(n1min);
+  op->n2 = choose_length(n2min);
+  if (op->n1 < 0 || op->n2 < 0 || op->n1 > kMaxFft || op->n2 > kMaxFft) {
+    delete op;
+    return fail(TF_EUNSUPPORTED, "embedding %d x %d exceeds the supported %d per axis", n1min,
+                n2min, kMaxFft);
+  }
+  op->nh = op->n1 / 2 + 1;
+  op->p1 = make_plan(op->n1);
+  op->p2 = make_plan(op->n2);
+  op->rows_tile = dt == TF_F32 ? 8 : 4;
+  op->cols_tile = dt == TF_F32 ? 8 : 4;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  tf_status st = TF_OK;
+  double* d_z = nullptr;
+  double* d_tab = nullptr;
+  double2* d_ht = nullptr;
+  double2* d_spec64 = nullptr;
+  void* tw1_64 = nullptr;
+  void* tw2_64 = nullptr;
+  cudaError_t e;
+  const int64_t ntab = (int64_t)op->nz * n2min * n1min;
+  const int64_t nht = (int64_t)op->nz * n2min * op->nh;
+  const int64_t nspec = (int64_t)op->nz * op->n2 * op->nh;
+
+#define TF_TRY(call, what)                       \
+  do {                                           \
+    e = (call);                                  \
+    if (e != cudaSuccess) { st = cuda_fail(e, what); goto done; } \
+  } while (0)
+
+  if ((st = upload_twiddles(op->p1, dt, &op->tw1)) != TF_OK) goto done;
+  if ((st = upload_twiddles(op->p2, dt, &op->tw2)) != TF_OK) goto done;
+  if (dt == TF_F32) {
+    if ((st = upload_twiddles(op->p1, TF_F64, &tw1_64)) != TF_OK) goto done;
+    if ((st = upload_twiddles(op->p2, TF_F64, &tw2_64)) != TF_OK) goto done;
+  } else {
+    tw1_64 = op->tw1;
+    tw2_64 = op->tw2;
+  }
+  TF_TRY(cudaMalloc(&d_z, sizeof(double) * (op->nz + 1)), "cudaMalloc(z_edges)");
+  TF_TRY(cudaMemcpy(d_z, op->z_edges.data(), sizeof(double) * (op->nz + 1), cudaMemcpyHostToDevice),
+         "cudaMemcpy(z_edges)");
+  TF_TRY(cudaMalloc(&d_tab, sizeof(double) * ntab), "cudaMalloc(kernel table)");
+  TF_TRY(cudaMalloc(&d_ht, sizeof(double2) * nht), "cudaMalloc(row spectra)");
+  TF_TRY(cudaMalloc(&d_spec64, sizeof(double2) * nspec), "cudaMalloc(spectra)");
+  {
+    tfk::TableArgs ta;
+    ta.kind = kind; ta.n1min = n1min; ta.n2min = n2min; ta.nz = op->nz;
+    ta.nx = op->nx; ta.ny = op->ny; ta.pxl = op->pxl; ta.pyl = op->pyl;
+    ta.dx = op->dx; ta.dy = op->dy; ta.station_z = op->station_z; ta.z_edges = d_z;
+    const double I = inc * 3.14159265358979323846 / 180.0, D = dec * 3.14159265358979323846 / 180.0;
+    ta.fx = cos(I) * cos(D); ta.fy = cos(I) * sin(D); ta.fz = sin(I); ta.field = field;
+    ta.out = d_tab;
+    TF_TRY(tfk::launch_table(ta, s), "kernel table launch");
+
+    tfk::RowsR2C<double> ra;
+    ra.src = d_tab; ra.src_ld = 0; ra.row_len = n1min; ra.nrows = op->nz * n2min;
+    ra.seq_off = 0; ra.scale = nullptr; ra.dst = d_ht; ra.dst_ld = 0; ra.nh = op->nh;
+    ra.plan = op->p1.plan; ra.tw = (const double2*)tw1_64;
+    TF_TRY(tfk::launch_rows_r2c<double>(ra, 1, 4, s), "row FFT of kernel table");
+
+    tfk::SpecArgs sa;
+    sa.ht = d_ht; sa.n2min = n2min; sa.nh = op->nh; sa.nz = op->nz;
+    sa.scale = 1.0 / ((double)op->n1 * op->n2);
+    sa.spec = d_spec64; sa.plan = op->p2.plan; sa.tw = (const double2*)tw2_64;
+    TF_TRY(tfk::launch_spectrum(sa, 4, s), "column FFT of kernel table");
+  }
+  if (dt == TF_F64) {
+    op->spec = d_spec64;
+    d_spec64 = nullptr;
+  } else {
+    TF_TRY(cudaMalloc(&op->spec, sizeof(float2) * nspec), "cudaMalloc(spectra f32)");
+    TF_TRY(tfk::launch_to_f32(d_spec64, (float2*)op->spec, nspec, s), "spectra rounding");
+  }
+  TF_TRY(cudaStreamSynchronize(s), "spectra set-up");
+  if ((st = alloc_workspace(op, default_chunk(op))) != TF_OK) goto done;
+
+done:
+#undef TF_TRY
+  cudaFree(d_z);
+  cudaFree(d_tab);
+  cudaFree(d_ht);
+  cudaFree(d_spec64);
+  if (dt == TF_F32) { cudaFree(tw1_64); cudaFree(tw2_64); }
+  if (st != TF_OK) { free_op(op); return st; }
+  *out = op;
+  return TF_OK;
+}
+
+cudaEvent_t take_event(tf_op* op) {
+  if (!op->pool.empty()) { cudaEvent_t e = op->pool.back(); op->pool.pop_back(); return e; }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Runs one stage launch, bracketed by profiling events when enabled.
+template <class F>
+cudaError_t stage(tf_op* op, int id, int64_t cols, cudaStream_t s, F&& launch) {
+  if (!op->prof) return launch();
+  tf_op::Rec r{id, cols, take_event(op), take_event(op)};
+  cudaEventRecord(r.a, s);
+  cudaError_t e = launch();
+  cudaEventRecord(r.b, s);
+  op->recs.push_back(r);
+  return e;
+}
+
+tf_status check_op(const tf_op* op) {
+  if (!op) return fail(TF_EINVAL, "op is NULL");
+  return TF_OK;
+}
+
+template <typename T>
+tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int64_t ldd,
+                       const T* cs, const T* rs, cudaStream_t s) {
+  typedef typename CT<T>::C C;
+  C* w1 = (C*)op->w1;
+  C* w2 = (C*)op->w2;
+  const C* tw1 = (const C*)op->tw1;
+  const C* tw2 = (const C*)op->tw2;
+  for (int64_t c0 = 0; c0 < B; c0 += op->chunk) {
+    const int cb = (int)std::min<int64_t>(op->chunk, B - c0);
+    tfk::RowsR2C<T> a;
+    a.src = X + c0 * ldx; a.src_ld = ldx; a.row_len = op->nx; a.nrows = op->nz * op->ny;
+    a.seq_off = 0; a.scale = cs; a.dst = w1; a.dst_ld = op->w1_per_col(); a.nh = op->nh;
+    a.plan = op->p1.plan; a.tw = tw1;
+    cudaError_t e = stage(op, 0, cb, s, [&] { return tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
+    tfk::ColsFwd<T> b;
+    b.z = w1; b.z_ld = op->w1_per_col(); b.spec = (const C*)op->spec; b.s = w2;
+    b.s_ld = op->w2_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
+    b.plan = op->p2.plan; b.tw = tw2;
+    e = stage(op, 1, cb, s, [&] { return tfk::launch_cols_fwd<T>(b, cb, op->cols_tile, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "cols_fwd launch");
+    tfk::RowsC2R<T> c;
+    c.src = w2; c.src_ld = op->w2_per_col(); c.nh = op->nh; c.nrows = op->sy;
+    c.dst = D + c0 * ldd; c.dst_ld = ldd; c.out_len = op->sx; c.seq_off = op->nx - 1;
+    c.scale = rs; c.plan = op->p1.plan; c.tw = tw1;
+    e = stage(op, 2, cb, s, [&] { return tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "rows_c2r launch");
+  }
+  return TF_OK;
+}
+
+template <typename T>
+tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int64_t ldx,
+                       const T* cs, const T* rs, cudaStream_t s) {
+  typedef typename CT<T>::C C;
+  C* w1 = (C*)op->w1;
+  C* w2 = (C*)op->w2;
+  const C* tw1 = (const C*)op->tw1;
+  const C* tw2 = (const C*)op->tw2;
+  for (int64_t c0 = 0; c0 < B; c0 += op->chunk) {
+    const int cb = (int)std::min<int64_t>(op->chunk, B - c0);
+    tfk::RowsR2C<T> a;
+    a.src = Y + c0 * ldy; a.src_ld = ldy; a.row_len = op->sx; a.nrows = op->sy;
+    a.seq_off = op->nx - 1; a.scale = rs; a.dst = w2; a.dst_ld = op->w2_per_col();
+    a.nh = op->nh; a.plan = op->p1.plan; a.tw = tw1;
+    cudaError_t e = stage(op, 3, cb, s, [&] { return tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
+    tfk::ColsAdj<T> b;
+    b.z = w2; b.z_ld = op->w2_per_col(); b.spec = (const C*)op->spec; b.u = w1;
+    b.u_ld = op->w1_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
+    b.plan = op->p2.plan; b.tw = tw2;
+    e = stage(op, 4, cb, s, [&] { return tfk::launch_cols_adj<T>(b, cb, op->cols_tile, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "cols_adj launch");
+    tfk::RowsC2R<T> c;
+    c.src = w1; c.src_ld = op->w1_per_col(); c.nh = op->nh; c.nrows = op->nz * op->ny;
+    c.dst = X + c0 * ldx; c.dst_ld = ldx; c.out_len = op->nx; c.seq_off = 0; c.scale = cs;
+    c.plan = op->p1.plan; c.tw = tw1;
+    e = stage(op, 5, cb, s, [&] { return tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "rows_c2r launch");
+  }
+  return TF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tf_status tf_create_gravity(const tf_grid* grid, tf_dtype dtype, tf_stream stream, tf_op** out) {
+  return create_common(grid, 0, 90.0, 0.0, 1.0, dtype, stream, out);
+}
+
+tf_status tf_create_magnetic(const tf_grid* grid, double inc_deg, double dec_deg,
+                             double field_nt, tf_dtype dtype, tf_stream stream, tf_op** out) {
+  return create_common(grid, 1, inc_deg, dec_deg, field_nt, dtype, stream, out);
+}
+
+tf_status tf_destroy(tf_op* op) {
+  if (!op) return TF_OK;
+  cudaDeviceSynchronize();
+  free_op(op);
+  return TF_OK;
+}
+
+tf_status tf_dims(const tf_op* op, int64_t* m, int64_t* n) {
+  if (check_op(op)) return TF_EINVAL;
+  if (m) *m = op->m();
+  if (n) *n = op->n();
+  return TF_OK;
+}
+
+tf_status tf_fft_dims(const tf_op* op, int* n1, int* n2) {
+  if (check_op(op)) return TF_EINVAL;
+  if (n1) *n1 = op->n1;
+  if (n2) *n2 = op->n2;
+  return TF_OK;
+}
+
+tf_status tf_matmat(tf_op* op, int64_t B, const void* X, int64_t ldx, void* D, int64_t ldd,
+                    const void* colscale, const void* rowscale, tf_stream stream) {
+  if (check_op(op)) return TF_EINVAL;
+  if (B < 0) return fail(TF_EINVAL, "B must be >= 0");
+  if (B == 0) return TF_OK;
+  if (!X || !D) return fail(TF_EINVAL, "X and D must be non-NULL");
+  if (ldx < op->n() || ldd < op->m())
+    return fail(TF_EINVAL, "ldx (%lld) must be >= n (%lld) and ldd (%lld) >= m (%lld)",
+                (long long)ldx, (long long)op->n(), (long long)ldd, (long long)op->m());
+  cudaStream_t s = (cudaStream_t)stream;
+  if (op->dtype == TF_F32)
+    return forward_impl<float>(op, B, (const float*)X, ldx, (float*)D, ldd,
+                               (const float*)colscale, (const float*)rowscale, s);
+  return forward_impl<double>(op, B, (const double*)X, ldx, (double*)D, ldd,
+                              (const double*)colscale, (const double*)rowscale, s);
+}
+
+tf_status tf_rmatmat(tf_op* op, int64_t B, const void* Y, int64_t ldy, void* X, int64_t ldx,
+                     const void* colscale, const void* rowscale, tf_stream stream) {
+  if (check_op(op)) return TF_EINVAL;
+  if (B < 0) return fail(TF_EINVAL, "B must be >= 0");
+  if (B == 0) return TF_OK;
+  if (!X || !Y) return fail(TF_EINVAL, "Y and X must be non-NULL");
+  if (ldy < op->m() || ldx < op->n())
+    return fail(TF_EINVAL, "ldy (%lld) must be >= m (%lld) and ldx (%lld) >= n (%lld)",
+                (long long)ldy, (long long)op->m(), (long long)ldx, (long long)op->n());
+  cudaStream_t s = (cudaStream_t)stream;
+  if (op->dtype == TF_F32)
+    return adjoint_impl<float>(op, B, (const float*)Y, ldy, (float*)X, ldx,
+                               (const float*)colscale, (const float*)rowscale, s);
+  return adjoint_impl<double>(op, B, (const double*)Y, ldy, (double*)X, ldx,
+                              (const double*)colscale, (const double*)rowscale, s);
+}
+
+tf_status tf_matvec(tf_op* op, const void* x, void* d, const void* colscale,
+                    const void* rowscale, tf_stream stream) {
+  if (check_op(op)) return TF_EINVAL;
+  return tf_matmat(op, 1, x, op->n(), d, op->m(), colscale, rowscale, stream);
+}
+
+tf_status tf_rmatvec(tf_op* op, const void* y, void* x, const void* colscale,
+                     const void* rowscale, tf_stream stream) {
+  if (check_op(op)) return TF_EINVAL;
+  return tf_rmatmat(op, 1, y, op->m(), x, op->n(), colscale, rowscale, stream);
+}
+
+tf_status tf_get_spectra(const tf_op* op, void* dst, int64_t bytes, tf_stream stream) {
+  if (check_op(op)) return TF_EINVAL;
+  const int64_t need = (int64_t)op->nz * op->n2 * op->nh * (int64_t)op->csize();
+  if (!dst || bytes != need)
+    return fail(TF_EINVAL, "dst must hold exactly %lld bytes", (long long)need);
+  cudaError_t e = cudaMemcpyAsync(dst, op->spec, (size_t)need, cudaMemcpyDefault,
+                                  (cudaStream_t)stream);
+  return e == cudaSuccess ? TF_OK : cuda_fail(e, "cudaMemcpyAsync(spectra)");
+}
+
+tf_status tf_set_tuning(tf_op* op, int rows_tile, int cols_tile, int64_t chunk_cols) {
+  if (check_op(op)) return TF_EINVAL;
+  auto ok_tile = [](int t) { return t == 0 || t == 4 || t == 8 || t == 16; };
+  if (!ok_tile(rows_tile) || !ok_tile(cols_tile) || chunk_cols < 0)
+    return fail(TF_EINVAL, "tiles must be 0, 4, 8 or 16 and chunk_cols >= 0");
+  const int rt = rows_tile ? rows_tile : op->rows_tile;
+  const int ct = cols_tile ? cols_tile : op->cols_tile;
+  const size_t lim = 227 * 1024;
+  if (tfk::smem_rows(op->n1, op->p1.plan.tw_count, rt, op->csize()) > lim ||
+      tfk::smem_cols(op->n2, op->p2.plan.tw_count, ct, op->csize()) > lim)
+    return fail(TF_EUNSUPPORTED, "tile needs more than 227 KB of shared memory");
+  op->rows_tile = rt;
+  op->cols_tile = ct;
+  if (chunk_cols && chunk_cols != op->chunk) {
+    cudaDeviceSynchronize();
+    return alloc_workspace(op, chunk_cols);
+  }
+  return TF_OK;
+}
+
+tf_status tf_get_tuning(const tf_op* op, int* rows_tile, int* cols_tile, int64_t* chunk_cols) {
+  if (check_op(op)) return TF_EINVAL;
+  if (rows_tile) *rows_tile = op->rows_tile;
+  if (cols_tile) *cols_tile = op->cols_tile;
+  if (chunk_cols) *chunk_cols = op->chunk;
+  return TF_OK;
+}
+
+tf_status tf_profile_enable(tf_op* op, int enable) {
+  if (check_op(op)) return TF_EINVAL;
+  for (auto& r : op->recs) { cudaEventSynchronize(r.b); op->pool.push_back(r.a); op->pool.push_back(r.b); }
+  op->recs.clear();
+  op->prof = enable != 0;
+  return TF_OK;
+}
+
+tf_status tf_profile_read(tf_op* op, double* ms, int64_t* launches, int64_t* columns) {
+  if (check_op(op)) return TF_EINVAL;
+  if (!ms || !launches || !columns) return fail(TF_EINVAL, "output arrays must be non-NULL");
+  for (int i = 0; i < kStages; ++i) { ms[i] = 0; launches[i] = 0; columns[i] = 0; }
+  for (auto& r : op->recs) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float t = 0;
+    e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    ms[r.stage] += t;
+    launches[r.stage] += 1;
+    columns[r.stage] += r.cols;
+  }
+  return TF_OK;
+}
+
+const char* tf_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// Mixed-radix Stockham FFT engine staged through shared memory (device code).
+//
+// The 2-D FFTs of App. A ("the 2DFFT of W is computed as 1DFFT((1DFFT(W))^T)^T") are
+// evaluated here as batches of 1-D transforms: a CTA holds TB independent sequences of
+// length N as a [N][ld] array (sequence index fastest), and every radix-R pass moves
+// each element once through registers (load R values at stride N/R, twiddle, radix-R
+// butterfly, store with Stockham's self-sorting index).  The first pass may read its
+// input through a caller functor (global memory, zero padding, a spectral product) and
+// the last pass may write through one (a layer accumulation, a windowed global store),
+// so that those steps cost no extra shared-memory round trip.
+//
+// Forward transforms use exp(-2 pi i n k / N); inverse transforms use the conjugate and
+// are unnormalised (the 1/(N1 N2) factor is folded into the stored layer spectra).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tfk {
+
+template <typename T> struct CT;
+template <> struct CT<float> { typedef float2 C; };
+template <> struct CT<double> { typedef double2 C; };
+
+template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+  C r; r.x = a; r.y = b; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C mul_mi(C a) {
+  return INV ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+
+// cos / sin of 2 pi m / R for the odd radices (mathematical constants, 25 digits)
+template <int R> __device__ __forceinline__ double cs_cos(int m);
+template <int R> __device__ __forceinline__ double cs_sin(int m);
+template <> __device__ __forceinline__ double cs_cos<3>(int m) { return -0.5; }
+template <> __device__ __forceinline__ double cs_sin<3>(int m) { return m == 1 ? 0.8660254037844386467637232 : -0.8660254037844386467637232; }
+template <> __device__ __forceinline__ double cs_cos<5>(int m) {
+  return (m == 1 || m == 4) ? 0.3090169943749474241022934 : -0.8090169943749474241022934;
+}
+template <> __device__ __forceinline__ double cs_sin<5>(int m) {
+  return m == 1 ? 0.9510565162951535721164393 : m == 2 ? 0.5877852522924731291687060
+       : m == 3 ? -0.5877852522924731291687060 : -0.9510565162951535721164393;
+}
+template <> __device__ __forceinline__ double cs_cos<7>(int m) {
+  return (m == 1 || m == 6) ? 0.6234898018587335305250049
+       : (m == 2 || m == 5) ? -0.2225209339563144042889026 : -0.9009688679024191262361023;
+}
+template <> __device__ __forceinline__ double cs_sin<7>(int m) {
+  return m == 1 ? 0.7818314824680298087084445 : m == 2 ? 0.9749279121818236070181317
+       : m == 3 ? 0.4338837391175581204757683 : m == 4 ? -0.4338837391175581204757683
+       : m == 5 ? -0.9749279121818236070181317 : -0.7818314824680298087084445;
+}
+
+// Odd-radix DFT from the symmetric/antisymmetric pairs a_n +- a_{R-n}.
+template <int R, bool INV, typename C> __device__ __forceinline__ void dft_odd(C* v) {
+  typedef decltype(C::x) T;
+  constexpr int H = (R - 1) / 2;
+  C s[H + 1], d[H + 1];
+  C y0 = v[0];
+#pragma unroll
+  for (int n = 1; n <= H; ++n) {
+    s[n] = cadd(v[n], v[R - n]);
+    d[n] = csub(v[n], v[R - n]);
+    y0 = cadd(y0, s[n]);
+  }
+  C out[R];
+  out[0] = y0;
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    C A = v[0], B = mk<C>(T(0), T(0));
+#pragma unroll
+    for (int n = 1; n <= H; ++n) {
+      const T c = T(cs_cos<R>((n * k) % R));
+      const T sn = T(cs_sin<R>((n * k) % R));
+      A = mk<C>(A.x + c * s[n].x, A.y + c * s[n].y);
+      B = mk<C>(B.x + sn * d[n].x, B.y + sn * d[n].y);
+    }
+    // forward: y_k = A - iB, y_{R-k} = A + iB ; inverse: signs swapped
+    const C iB = mk<C>(-B.y, B.x);
+    out[k] = INV ? cadd(A, iB) : csub(A, iB);
+    out[R - k] = INV ? csub(A, iB) : cadd(A, iB);
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = out[k];
+}
+
+template <int R, bool INV, typename C> struct Dft;
+template <bool INV, typename C> struct Dft<2, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b); v[1] = csub(a, b);
+  }
+};
+template <bool INV, typename C> struct Dft<4, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    C s13 = cadd(v[1], v[3]), d13 = mul_mi<INV>(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13); v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13); v[3] = csub(d02, d13);
+  }
+};
+template <bool INV, typename C> struct Dft<8, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    typedef decltype(C::x) T;
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, INV, C>::run(e);
+    Dft<4, INV, C>::run(o);
+    const T h = T(0.7071067811865475244008444);
+    // w8^1 = h(1 -+ i), w8^2 = -+i, w8^3 = h(-1 -+ i)
+    C o1 = INV ? mk<C>(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+               : mk<C>(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+    C o2 = mul_mi<INV>(o[2]);
+    C o3 = INV ? mk<C>(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+               : mk<C>(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+  }
+};
+template <bool INV, typename C> struct Dft<3, INV, C> {
+  static __device__ __forceinline__ void run(C* v) { dft_odd<3, INV>(v); }
+};
+template <bool INV, typename C> struct Dft<5, INV, C> {
+  static __device__ __forceinline__ void run(C* v) { dft_odd<5, INV>(v); }
+};
+template <bool INV, typename C> struct Dft<7, INV, C> {
+  static __device__ __forceinline__ void run(C* v) { dft_odd<7, INV>(v); }
+};
+
+constexpr int kMaxPass = 16;
+
+// A 1-D transform of length n as np radix passes.  Pass p has radix radix[p], stride
+// ns[p] = product of the earlier radices, and its twiddles w^(r k), k < ns[p],
+// 1 <= r < radix[p], stored at tw[tw_off[p] + k (radix[p]-1) + r - 1] with
+// w = exp(-2 pi i / (ns[p] radix[p])).  The table holds n - 1 entries in total.
+struct FftPlan {
+  int n;
+  int np;
+  int tw_count;
+  int radix[kMaxPass];
+  int ns[kMaxPass];
+  int tw_off[kMaxPass];
+};
+
+// One Stockham pass over TB = 2^tbs interleaved sequences.
+template <int R, bool INV, typename C, class L, class S>
+__device__ __forceinline__ void fft_pass(int nb, int Ns, int tbs, const C* __restrict__ tw,
+                                         const L& load, const S& store) {
+  const int tbm = (1 << tbs) - 1;
+  const int total = nb << tbs;
+  for (int u = threadIdx.x; u < total; u += blockDim.x) {
+    const int j = u >> tbs, b = u & tbm;
+    const int k = j % Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = load(j + r * nb, b);
+    if (Ns > 1) {
+      const C* t = tw + k * (R - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = t[r - 1];
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    Dft<R, INV, C>::run(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) store(base + r * Ns, b, v[r]);
+  }
+}
+
+template <bool INV, typename C, class L, class S>
+__device__ __forceinline__ void fft_pass_any(int R, int nb, int Ns, int tbs, const C* tw,
+                                             const L& load, const S& store) {
+  switch (R) {
+    case 2: fft_pass<2, INV>(nb, Ns, tbs, tw, load, store); break;
+    case 3: fft_pass<3, INV>(nb, Ns, tbs, tw, load, store); break;
+    case 4: fft_pass<4, INV>(nb, Ns, tbs, tw, load, store); break;
+    case 5: fft_pass<5, INV>(nb, Ns, tbs, tw, load, store); break;
+    case 7: fft_pass<7, INV>(nb, Ns, tbs, tw, load, store); break;
+    default: fft_pass<8, INV>(nb, Ns, tbs, tw, load, store); break;
+  }
+}
+
+template <typename C> struct SmemLoad {
+  const C* p; int ld;
+  __device__ __forceinline__ C operator()(int idx, int b) const { return p[idx * ld + b]; }
+};
+template <typename C> struct SmemStore {
+  C* p; int ld;
+  __device__ __forceinline__ void operator()(int idx, int b, C v) const { p[idx * ld + b] = v; }
+};
+
+// Full transform: pass 0 reads through `first`, the last pass writes through `last`,
+// intermediate passes ping-pong between bufA (even passes write) and bufB (odd).
+// Every pass ends with __syncthreads().  Callers synchronise before the first pass
+// if `first` reads shared memory written earlier.
+template <bool INV, typename C, class L0, class SL>
+__device__ __forceinline__ void fft_run(const FftPlan& P, const C* tw, C* bufA, C* bufB, int ld,
+                                        int tbs, const L0& first, const SL& last) {
+  for (int p = 0; p < P.np; ++p) {
+    const int R = P.radix[p];
+    const int nb = P.n / R;
+    const int Ns = P.ns[p];
+    const C* twp = tw + P.tw_off[p];
+    SmemLoad<C> sl{(p & 1) ? bufA : bufB, ld};
+    SmemStore<C> ss{(p & 1) ? bufB : bufA, ld};
+    const bool f = (p == 0), l = (p == P.np - 1);
+    if (f && l) fft_pass_any<INV>(R, nb, Ns, tbs, twp, first, last);
+    else if (f) fft_pass_any<INV>(R, nb, Ns, tbs, twp, first, ss);
+    else if (l) fft_pass_any<INV>(R, nb, Ns, tbs, twp, sl, last);
+    else fft_pass_any<INV>(R, nb, Ns, tbs, twp, sl, ss);
+    __syncthreads();
+  }
+}
+
+}  // namespace tfk

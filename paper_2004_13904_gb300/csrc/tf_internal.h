@@ -1,0 +1,76 @@
+// Internal launchers shared by the C-ABI layer and the kernels (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tf_fft.cuh"
+
+namespace tfk {
+
+// Rows stage, real -> half spectrum (App. A: 1-D FFTs along x of the embedded rows).
+// Row rho of column b holds row_len reals at src + b*src_ld + rho*row_len; they are
+// scaled by scale[rho*row_len + n] (if non-null), placed at [seq_off, seq_off+row_len)
+// of a zero sequence of length plan.n, transformed, and the nh = n/2+1 outputs are
+// written to dst + b*dst_ld + rho*nh.  Two rows share one complex transform.
+template <typename T> struct RowsR2C {
+  const T* src; int64_t src_ld; int row_len; int nrows; int seq_off; const T* scale;
+  typename CT<T>::C* dst; int64_t dst_ld; int nh;
+  FftPlan plan; const typename CT<T>::C* tw;
+};
+
+// Rows stage, half spectrum -> real window: inverse of the above; outputs sequence
+// entries [seq_off, seq_off+out_len) times scale[rho*out_len + i] to dst.
+template <typename T> struct RowsC2R {
+  const typename CT<T>::C* src; int64_t src_ld; int nh; int nrows;
+  T* dst; int64_t dst_ld; int out_len; int seq_off; const T* scale;
+  FftPlan plan; const typename CT<T>::C* tw;
+};
+
+// Column stage of G x: for each k1 column, FFT along y of every layer's rows,
+// multiply-accumulate with the layer spectra (sum over layers in the frequency domain),
+// inverse FFT, keep rows [ny-1, ny-1+sy).
+template <typename T> struct ColsFwd {
+  const typename CT<T>::C* z; int64_t z_ld;       // [nz*ny][nh] per column
+  const typename CT<T>::C* spec;                  // [nz][n2][nh]
+  typename CT<T>::C* s; int64_t s_ld;             // [sy][nh] per column
+  int nh, ny, sy, nz;
+  FftPlan plan; const typename CT<T>::C* tw;
+};
+
+// Column stage of G^T y: FFT along y of the data rows placed at [ny-1, ny-1+sy), then
+// per layer multiply by the conjugate spectrum, inverse FFT, keep rows [0, ny).
+template <typename T> struct ColsAdj {
+  const typename CT<T>::C* z; int64_t z_ld;       // [sy][nh] per column
+  const typename CT<T>::C* spec;                  // [nz][n2][nh]
+  typename CT<T>::C* u; int64_t u_ld;             // [nz*ny][nh] per column
+  int nh, ny, sy, nz;
+  FftPlan plan; const typename CT<T>::C* tw;
+};
+
+struct TableArgs {
+  int kind;                // 0 gravity, 1 magnetic
+  int n1min, n2min, nz, nx, ny, pxl, pyl;
+  double dx, dy, station_z;
+  const double* z_edges;   // device, nz+1
+  double fx, fy, fz, field;  // magnetic: field direction and strength (nT)
+  double* out;             // [nz][n2min][n1min]
+};
+
+struct SpecArgs {
+  const double2* ht; int n2min; int nh; int nz; double scale;
+  double2* spec;           // [nz][n2][nh]
+  FftPlan plan; const double2* tw;
+};
+
+template <typename T> cudaError_t launch_rows_r2c(const RowsR2C<T>& a, int ncols, int tb, cudaStream_t s);
+template <typename T> cudaError_t launch_rows_c2r(const RowsC2R<T>& a, int ncols, int tb, cudaStream_t s);
+template <typename T> cudaError_t launch_cols_fwd(const ColsFwd<T>& a, int ncols, int tk, cudaStream_t s);
+template <typename T> cudaError_t launch_cols_adj(const ColsAdj<T>& a, int ncols, int tk, cudaStream_t s);
+cudaError_t launch_table(const TableArgs& a, cudaStream_t s);
+cudaError_t launch_spectrum(const SpecArgs& a, int tk, cudaStream_t s);
+cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t count, cudaStream_t s);
+
+size_t smem_rows(int n, int tw_count, int tb, size_t csize);
+size_t smem_cols(int n, int tw_count, int tk, size_t csize);
+
+}  // namespace tfk

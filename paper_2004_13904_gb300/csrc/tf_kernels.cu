@@ -1,0 +1,439 @@
+// CUDA kernels of the BTTB/BCCB products (App. A) and of the layer-spectra set-up.
+//
+// A forward product G x runs as three stages per chunk of columns:
+//   rows_r2c  : x rows (scaled by colscale, zero-embedded) -> 1-D FFT along x (half spectra)
+//   cols_fwd  : per k1 column: 1-D FFT along y of each layer, multiply by that layer's
+//               spectrum and accumulate over layers, inverse FFT along y, keep sy rows
+//   rows_c2r  : inverse FFT along x of the sy rows, keep the sx station window, scale
+// The transpose product G^T y runs rows_r2c (data rows), cols_adj (one forward FFT,
+// then per layer a conjugate-spectrum product and an inverse FFT), rows_c2r (model rows).
+#include <math.h>
+
+#include <algorithm>
+
+#include "tf_internal.h"
+
+namespace tfk {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
+template <> struct Log2<1> { static constexpr int value = 0; };
+
+__host__ __device__ inline int tw_pad(int count) { return (count + 1) & ~1; }
+
+template <typename C> __device__ __forceinline__ C czero() { return mk<C>(0, 0); }
+
+template <typename T, int TB>
+__global__ void __launch_bounds__(kThreads) k_rows_r2c(const RowsR2C<T> a) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  const int N = a.plan.n;
+  constexpr int ld = TB + 1;
+  C* bufA = tw + tw_pad(a.plan.tw_count);
+  C* bufB = bufA + N * ld;
+  for (int i = threadIdx.x; i < a.plan.tw_count; i += blockDim.x) tw[i] = a.tw[i];
+
+  const int pair0 = blockIdx.x * TB;
+  const T* src = a.src + (int64_t)blockIdx.y * a.src_ld;
+  // stage two real rows per complex sequence into bufB, rows of x contiguous in global
+  for (int u = threadIdx.x; u < TB * N; u += blockDim.x) {
+    const int pp = u / N, n = u - pp * N;
+    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+    const int e = n - a.seq_off;
+    T xa = T(0), xb = T(0);
+    if (e >= 0 && e < a.row_len) {
+      if (ra < a.nrows) {
+        const int64_t o = (int64_t)ra * a.row_len + e;
+        xa = src[o];
+        if (a.scale) xa *= a.scale[o];
+      }
+      if (rb < a.nrows) {
+        const int64_t o = (int64_t)rb * a.row_len + e;
+        xb = src[o];
+        if (a.scale) xb *= a.scale[o];
+      }
+    }
+    bufB[n * ld + pp] = mk<C>(xa, xb);
+  }
+  __syncthreads();
+  C* fin = ((a.plan.np - 1) & 1) ? bufB : bufA;
+  fft_run<false>(a.plan, tw, bufA, bufB, ld, Log2<TB>::value, SmemLoad<C>{bufB, ld},
+                 SmemStore<C>{fin, ld});
+  // split the packed transform into the two rows' half spectra
+  C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
+  const int nh = a.nh;
+  for (int u = threadIdx.x; u < TB * nh; u += blockDim.x) {
+    const int pp = u / nh, k = u - pp * nh;
+    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+    if (ra >= a.nrows) continue;
+    const C z = fin[k * ld + pp];
+    C zc = fin[(k ? N - k : 0) * ld + pp];
+    zc.y = -zc.y;
+    dst[(int64_t)ra * nh + k] = mk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
+    if (rb < a.nrows)
+      dst[(int64_t)rb * nh + k] = mk<C>(T(0.5) * (z.y - zc.y), T(-0.5) * (z.x - zc.x));
+  }
+}
+
+template <typename T, int TB>
+__global__ void __launch_bounds__(kThreads) k_rows_c2r(const RowsC2R<T> a) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  const int N = a.plan.n;
+  constexpr int ld = TB + 1;
+  C* bufA = tw + tw_pad(a.plan.tw_count);
+  C* bufB = bufA + N * ld;
+  for (int i = threadIdx.x; i < a.plan.tw_count; i += blockDim.x) tw[i] = a.tw[i];
+
+  const int pair0 = blockIdx.x * TB;
+  const int nh = a.nh;
+  const C* src = a.src + (int64_t)blockIdx.y * a.src_ld;
+  // pack two Hermitian half spectra into one complex sequence: Z = Xa + i Xb
+  for (int u = threadIdx.x; u < TB * nh; u += blockDim.x) {
+    const int pp = u / nh, k = u - pp * nh;
+    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+    C xa = ra < a.nrows ? src[(int64_t)ra * nh + k] : czero<C>();
+    C xb = rb < a.nrows ? src[(int64_t)rb * nh + k] : czero<C>();
+    const bool self = (k == 0) || (2 * k == N);
+    if (self) { xa.y = T(0); xb.y = T(0); }
+    bufB[k * ld + pp] = mk<C>(xa.x - xb.y, xa.y + xb.x);
+    if (!self) bufB[(N - k) * ld + pp] = mk<C>(xa.x + xb.y, xb.x - xa.y);
+  }
+  __syncthreads();
+  C* fin = ((a.plan.np - 1) & 1) ? bufB : bufA;
+  fft_run<true>(a.plan, tw, bufA, bufB, ld, Log2<TB>::value, SmemLoad<C>{bufB, ld},
+                SmemStore<C>{fin, ld});
+  T* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
+  const int L = a.out_len;
+  for (int u = threadIdx.x; u < TB * L; u += blockDim.x) {
+    const int pp = u / L, i = u - pp * L;
+    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+    if (ra >= a.nrows) continue;
+    const C z = fin[(a.seq_off + i) * ld + pp];
+    const int64_t oa = (int64_t)ra * L + i;
+    dst[oa] = a.scale ? z.x * a.scale[oa] : z.x;
+    if (rb < a.nrows) {
+      const int64_t ob = (int64_t)rb * L + i;
+      dst[ob] = a.scale ? z.y * a.scale[ob] : z.y;
+    }
+  }
+}
+
+template <typename T, int TK>
+__global__ void __launch_bounds__(kThreads) k_cols_fwd(const ColsFwd<T> a) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  const int N = a.plan.n;
+  C* bufA = tw + tw_pad(a.plan.tw_count);
+  C* bufB = bufA + N * TK;
+  C* acc = bufB + N * TK;
+  for (int i = threadIdx.x; i < a.plan.tw_count; i += blockDim.x) tw[i] = a.tw[i];
+  __syncthreads();
+
+  const int k0 = blockIdx.x * TK;
+  const int nh = a.nh, ny = a.ny, sy = a.sy;
+  const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
+  for (int r = 0; r < a.nz; ++r) {
+    const C* zr = z + (int64_t)r * ny * nh;
+    const C* gr = a.spec + (int64_t)r * N * nh;
+    const bool first_layer = (r == 0);
+    auto load = [=](int idx, int tk) -> C {
+      const int k1 = k0 + tk;
+      return (idx < ny && k1 < nh) ? zr[(int64_t)idx * nh + k1] : czero<C>();
+    };
+    auto mac = [=](int idx, int tk, C v) {
+      const int k1 = k0 + tk;
+      const C g = k1 < nh ? gr[(int64_t)idx * nh + k1] : czero<C>();
+      const C p = cmul(g, v);
+      C* d = acc + idx * TK + tk;
+      *d = first_layer ? p : cadd(*d, p);
+    };
+    fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, mac);
+  }
+  C* s = a.s + (int64_t)blockIdx.y * a.s_ld;
+  auto store = [=](int idx, int tk, C v) {
+    const int j = idx - (ny - 1), k1 = k0 + tk;
+    if (j >= 0 && j < sy && k1 < nh) s[(int64_t)j * nh + k1] = v;
+  };
+  fft_run<true>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, SmemLoad<C>{acc, TK}, store);
+}
+
+template <typename T, int TK>
+__global__ void __launch_bounds__(kThreads) k_cols_adj(const ColsAdj<T> a) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  const int N = a.plan.n;
+  C* bufA = tw + tw_pad(a.plan.tw_count);
+  C* bufB = bufA + N * TK;
+  C* acc = bufB + N * TK;
+  for (int i = threadIdx.x; i < a.plan.tw_count; i += blockDim.x) tw[i] = a.tw[i];
+  __syncthreads();
+
+  const int k0 = blockIdx.x * TK;
+  const int nh = a.nh, ny = a.ny, sy = a.sy;
+  const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
+  auto load = [=](int idx, int tk) -> C {
+    const int j = idx - (ny - 1), k1 = k0 + tk;
+    return (j >= 0 && j < sy && k1 < nh) ? z[(int64_t)j * nh + k1] : czero<C>();
+  };
+  fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, SmemStore<C>{acc, TK});
+  C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
+  for (int r = 0; r < a.nz; ++r) {
+    const C* gr = a.spec + (int64_t)r * N * nh;
+    C* ur = u + (int64_t)r * ny * nh;
+    auto prod = [=](int idx, int tk) -> C {
+      const int k1 = k0 + tk;
+      return k1 < nh ? cmulc(acc[idx * TK + tk], gr[(int64_t)idx * nh + k1]) : czero<C>();
+    };
+    auto store = [=](int idx, int tk, C v) {
+      const int k1 = k0 + tk;
+      if (idx < ny && k1 < nh) ur[(int64_t)idx * nh + k1] = v;
+    };
+    fft_run<true>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, prod, store);
+  }
+}
+
+// ---- layer spectra set-up (FP64) ------------------------------------------------------
+
+// ln(a + r), r = sqrt(a^2 + rest2), without cancellation for a < 0
+__device__ __forceinline__ double log_plus(double a, double rest2, double r) {
+  return a >= 0.0 ? log(a + r) : log(rest2 / (r - a));
+}
+
+// Vertical attraction (m/s^2 per kg/m^3 / gamma) of the prism [x1,x2]x[y1,y2]x[z1,z2]
+// relative to the station (z down): sum over corners of
+// (-1)^(i+j+k) [x ln(y+R) + y ln(x+R) - z atan2(xy, zR)].
+__device__ double prism_gz(double x1, double x2, double y1, double y2, double z1, double z2) {
+  const double xs[2] = {x1, x2}, ys[2] = {y1, y2}, zs[2] = {z1, z2};
+  double acc = 0.0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const double x = xs[i], y = ys[j], z = zs[k];
+        const double x2_ = x * x, y2_ = y * y, z2_ = z * z;
+        const double R = sqrt(x2_ + y2_ + z2_);
+        const double f = x * log_plus(y, x2_ + z2_, R) + y * log_plus(x, y2_ + z2_, R) -
+                         z * atan2(x * y, z * R);
+        acc += ((i + j + k) & 1) ? -f : f;
+      }
+  return acc;
+}
+
+// Total-field anomaly factor f.T.f of the prism's second-derivative tensor of
+// Int 1/R dV (Poisson's relation for a uniformly induced prism).
+__device__ double prism_ftf(double x1, double x2, double y1, double y2, double z1, double z2,
+                            double fx, double fy, double fz) {
+  const double xs[2] = {x1, x2}, ys[2] = {y1, y2}, zs[2] = {z1, z2};
+  double txx = 0, tyy = 0, tzz = 0, txy = 0, txz = 0, tyz = 0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const double x = xs[i], y = ys[j], z = zs[k];
+        const double x2_ = x * x, y2_ = y * y, z2_ = z * z;
+        const double R = sqrt(x2_ + y2_ + z2_);
+        // product of per-axis signs, +1 at the upper limit of each axis
+        const double cu = ((i + j + k) & 1) ? 1.0 : -1.0;
+        txx -= cu * atan(y * z / (x * R));
+        tyy -= cu * atan(x * z / (y * R));
+        tzz -= cu * atan2(x * y, z * R);
+        txy += cu * log_plus(z, x2_ + y2_, R);
+        txz += cu * log_plus(y, x2_ + z2_, R);
+        tyz += cu * log_plus(x, y2_ + z2_, R);
+      }
+  return fx * fx * txx + fy * fy * tyy + fz * fz * tzz +
+         2.0 * (fx * fy * txy + fx * fz * txz + fy * fz * tyz);
+}
+
+__global__ void k_table(const TableArgs a) {
+  const int64_t total = (int64_t)a.nz * a.n2min * a.n1min;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e % a.n1min);
+    const int t = (int)((e / a.n1min) % a.n2min);
+    const int r = (int)(e / ((int64_t)a.n1min * a.n2min));
+    // cell centre minus station for table entry (s, t)
+    const double cx = -(double)(s - (a.nx - 1) + a.pxl) * a.dx;
+    const double cy = -(double)(t - (a.ny - 1) + a.pyl) * a.dy;
+    const double z1 = a.z_edges[r] - a.station_z, z2 = a.z_edges[r + 1] - a.station_z;
+    const double x1 = cx - 0.5 * a.dx, x2 = cx + 0.5 * a.dx;
+    const double y1 = cy - 0.5 * a.dy, y2 = cy + 0.5 * a.dy;
+    double v;
+    if (a.kind == 0) {
+      // gamma [m^3/(kg s^2)] * 1000 [kg/m^3 per g/cc] * 1e5 [mGal per m/s^2]
+      v = 6.67430e-3 * prism_gz(x1, x2, y1, y2, z1, z2);
+    } else {
+      v = a.field / (4.0 * 3.14159265358979323846) *
+          prism_ftf(x1, x2, y1, y2, z1, z2, a.fx, a.fy, a.fz);
+    }
+    a.out[e] = v;
+  }
+}
+
+template <int TK>
+__global__ void __launch_bounds__(kThreads) k_spectrum(const SpecArgs a) {
+  typedef double2 C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  const int N = a.plan.n;
+  C* bufA = tw + tw_pad(a.plan.tw_count);
+  C* bufB = bufA + N * TK;
+  for (int i = threadIdx.x; i < a.plan.tw_count; i += blockDim.x) tw[i] = a.tw[i];
+  __syncthreads();
+  const int k0 = blockIdx.x * TK, r = blockIdx.y, nh = a.nh, n2min = a.n2min;
+  const C* ht = a.ht + (int64_t)r * n2min * nh;
+  C* out = a.spec + (int64_t)r * N * nh;
+  const double sc = a.scale;
+  auto load = [=](int idx, int tk) -> C {
+    const int k1 = k0 + tk;
+    return (idx < n2min && k1 < nh) ? ht[(int64_t)idx * nh + k1] : czero<C>();
+  };
+  auto store = [=](int idx, int tk, C v) {
+    const int k1 = k0 + tk;
+    if (k1 < nh) out[(int64_t)idx * nh + k1] = cscale(v, sc);
+  };
+  fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, store);
+}
+
+__global__ void k_to_f32(const double2* __restrict__ src, float2* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+
+template <class K>
+cudaError_t prep(K kernel, size_t smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+
+size_t smem_rows(int n, int tw_count, int tb, size_t csize) {
+  return ((size_t)tw_pad(tw_count) + 2 * (size_t)n * (tb + 1)) * csize;
+}
+size_t smem_cols(int n, int tw_count, int tk, size_t csize) {
+  return ((size_t)tw_pad(tw_count) + 3 * (size_t)n * tk) * csize;
+}
+
+template <typename T, int TB>
+static cudaError_t rows_r2c_tb(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
+  const size_t sm = smem_rows(a.plan.n, a.plan.tw_count, TB, sizeof(typename CT<T>::C));
+  cudaError_t e = prep(k_rows_r2c<T, TB>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ceil_div((a.nrows + 1) / 2, TB), ncols);
+  k_rows_r2c<T, TB><<<grid, kThreads, sm, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int TB>
+static cudaError_t rows_c2r_tb(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
+  const size_t sm = smem_rows(a.plan.n, a.plan.tw_count, TB, sizeof(typename CT<T>::C));
+  cudaError_t e = prep(k_rows_c2r<T, TB>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ceil_div((a.nrows + 1) / 2, TB), ncols);
+  k_rows_c2r<T, TB><<<grid, kThreads, sm, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int TK>
+static cudaError_t cols_fwd_tk(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
+  const size_t sm = smem_cols(a.plan.n, a.plan.tw_count, TK, sizeof(typename CT<T>::C));
+  cudaError_t e = prep(k_cols_fwd<T, TK>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ceil_div(a.nh, TK), ncols);
+  k_cols_fwd<T, TK><<<grid, kThreads, sm, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int TK>
+static cudaError_t cols_adj_tk(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
+  const size_t sm = smem_cols(a.plan.n, a.plan.tw_count, TK, sizeof(typename CT<T>::C));
+  cudaError_t e = prep(k_cols_adj<T, TK>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ceil_div(a.nh, TK), ncols);
+  k_cols_adj<T, TK><<<grid, kThreads, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rows_r2c(const RowsR2C<T>& a, int ncols, int tb, cudaStream_t s) {
+  switch (tb) {
+    case 4: return rows_r2c_tb<T, 4>(a, ncols, s);
+    case 8: return rows_r2c_tb<T, 8>(a, ncols, s);
+    case 16: return rows_r2c_tb<T, 16>(a, ncols, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T>
+cudaError_t launch_rows_c2r(const RowsC2R<T>& a, int ncols, int tb, cudaStream_t s) {
+  switch (tb) {
+    case 4: return rows_c2r_tb<T, 4>(a, ncols, s);
+    case 8: return rows_c2r_tb<T, 8>(a, ncols, s);
+    case 16: return rows_c2r_tb<T, 16>(a, ncols, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T>
+cudaError_t launch_cols_fwd(const ColsFwd<T>& a, int ncols, int tk, cudaStream_t s) {
+  switch (tk) {
+    case 4: return cols_fwd_tk<T, 4>(a, ncols, s);
+    case 8: return cols_fwd_tk<T, 8>(a, ncols, s);
+    case 16: return cols_fwd_tk<T, 16>(a, ncols, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T>
+cudaError_t launch_cols_adj(const ColsAdj<T>& a, int ncols, int tk, cudaStream_t s) {
+  switch (tk) {
+    case 4: return cols_adj_tk<T, 4>(a, ncols, s);
+    case 8: return cols_adj_tk<T, 8>(a, ncols, s);
+    case 16: return cols_adj_tk<T, 16>(a, ncols, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_rows_r2c<float>(const RowsR2C<float>&, int, int, cudaStream_t);
+template cudaError_t launch_rows_r2c<double>(const RowsR2C<double>&, int, int, cudaStream_t);
+template cudaError_t launch_rows_c2r<float>(const RowsC2R<float>&, int, int, cudaStream_t);
+template cudaError_t launch_rows_c2r<double>(const RowsC2R<double>&, int, int, cudaStream_t);
+template cudaError_t launch_cols_fwd<float>(const ColsFwd<float>&, int, int, cudaStream_t);
+template cudaError_t launch_cols_fwd<double>(const ColsFwd<double>&, int, int, cudaStream_t);
+template cudaError_t launch_cols_adj<float>(const ColsAdj<float>&, int, int, cudaStream_t);
+template cudaError_t launch_cols_adj<double>(const ColsAdj<double>&, int, int, cudaStream_t);
+
+cudaError_t launch_table(const TableArgs& a, cudaStream_t s) {
+  const int64_t total = (int64_t)a.nz * a.n2min * a.n1min;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k_table<<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum(const SpecArgs& a, int tk, cudaStream_t s) {
+  (void)tk;
+  constexpr int TK = 4;
+  const size_t sm = ((size_t)tw_pad(a.plan.tw_count) + 2 * (size_t)a.plan.n * TK) * sizeof(double2);
+  cudaError_t e = prep(k_spectrum<TK>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ceil_div(a.nh, TK), a.nz);
+  k_spectrum<TK><<<grid, kThreads, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t count, cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::min<int64_t>((count + 255) / 256, 152 * 8);
+  k_to_f32<<<blocks, 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+}  // namespace tfk
