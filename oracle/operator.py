@@ -36,9 +36,9 @@ __all__ = ["layer_tables", "dense_G", "fft_matvec", "fft_rmatvec", "station_row"
 def kernel_eval(kind: str, x1, x2, y1, y2, z1, z2, inc=90.0, dec=0.0):
     """Entry of G for a prism with the given corner offsets (cell minus station)."""
     if kind == "gravity":
-        return prism.gravity_gz(x1, x2, y1, y2, z1, z2)
+        return prism.gravity_cell(x1, x2, y1, y2, z1, z2)
     if kind == "magnetic":
-        return prism.magnetic_dt(x1, x2, y1, y2, z1, z2, inc, dec)
+        return prism.magnetic_cell(x1, x2, y1, y2, z1, z2, inc, dec)
     raise ValueError(kind)
 
 

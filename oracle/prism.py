@@ -21,6 +21,16 @@ volume integrals of a point-source kernel over a right rectangular prism:
 
 Coordinates passed in are corner offsets ``cell corner - station`` in metres.  Units:
 gravity in mGal per g/cc, magnetic in nT per SI susceptibility.
+
+Numerical evaluation (the paper is silent on it): the closed forms sum eight corner
+terms of size ~R log R whose total is ~V/R^2 (gravity) or ~V/R^3 (magnetic), so they
+lose about (R/L)^3 ulps to cancellation at distance R from a cell of size L (7e-7
+relative error at 150 cells).  The cell entries used for G (``gravity_cell``,
+``magnetic_cell``) therefore take the closed form only within 2 L of the station and
+otherwise integrate the point-source kernel by tensor Gauss-Legendre quadrature: 14
+points per axis for 2 L <= D < 4 L, 8 for 4 L <= D < 8 L and 6 beyond (D = distance
+from the station to the cell centre, L = the longest cell side).  Against 40-digit
+evaluations of the closed form this keeps every entry within ~1e-13 relative.
 """
 from __future__ import annotations
 
@@ -103,3 +113,74 @@ def magnetic_dt(x1, x2, y1, y2, z1, z2, inc_deg: float, dec_deg: float,
     quad = (fx * fx * txx + fy * fy * tyy + fz * fz * tzz
             + 2.0 * (fx * fy * txy + fx * fz * txz + fy * fz * tyz))
     return field_nt / (4.0 * np.pi) * quad
+
+
+# --- cell entries: closed form near the station, Gauss-Legendre quadrature far -------
+NEAR = 2.0
+MID = 4.0
+FAR = 8.0
+
+
+def _gauss_points(n: int):
+    t, w = np.polynomial.legendre.leggauss(n)
+    return t, w
+
+
+def _quadrature(x1, x2, y1, y2, z1, z2, n, integrand):
+    """Tensor Gauss-Legendre rule with n points per axis over each prism (arrays)."""
+    t, w = _gauss_points(n)
+    cx, hx = 0.5 * (x1 + x2), 0.5 * (x2 - x1)
+    cy, hy = 0.5 * (y1 + y2), 0.5 * (y2 - y1)
+    cz, hz = 0.5 * (z1 + z2), 0.5 * (z2 - z1)
+    total = 0.0
+    for i in range(n):
+        x = cx + hx * t[i]
+        for j in range(n):
+            y = cy + hy * t[j]
+            wij = w[i] * w[j]
+            for k in range(n):
+                z = cz + hz * t[k]
+                total = total + (wij * w[k]) * integrand(x, y, z)
+    return total * hx * hy * hz
+
+
+def _hybrid(x1, x2, y1, y2, z1, z2, closed, integrand):
+    x1, x2, y1, y2, z1, z2 = np.broadcast_arrays(*[np.asarray(v, np.float64)
+                                                   for v in (x1, x2, y1, y2, z1, z2)])
+    cx, cy, cz = 0.5 * (x1 + x2), 0.5 * (y1 + y2), 0.5 * (z1 + z2)
+    L = np.maximum(np.maximum(x2 - x1, y2 - y1), z2 - z1)
+    D = np.sqrt(cx * cx + cy * cy + cz * cz)
+    out = np.empty(x1.shape)
+    groups = [(D < NEAR * L, None), ((D >= NEAR * L) & (D < MID * L), 14),
+              ((D >= MID * L) & (D < FAR * L), 8), (D >= FAR * L, 6)]
+    for mask, n in groups:
+        if not np.any(mask):
+            continue
+        args = [v[mask] for v in (x1, x2, y1, y2, z1, z2)]
+        out[mask] = closed(*args) if n is None else _quadrature(*args, n, integrand)
+    return out if out.shape else float(out)
+
+
+def gravity_cell(x1, x2, y1, y2, z1, z2):
+    """Entry of G for gravity (mGal per g/cc): Int z/R^3 dV, accurate at any distance."""
+    def f(x, y, z):
+        r2 = x * x + y * y + z * z
+        return z / (r2 * np.sqrt(r2))
+    return GRAV_SCALE * _hybrid(x1, x2, y1, y2, z1, z2, gravity_unit, f)
+
+
+def magnetic_cell(x1, x2, y1, y2, z1, z2, inc_deg: float, dec_deg: float,
+                  field_nt: float = FIELD_NT):
+    """Entry of G for the total-field anomaly (nT per SI), accurate at any distance."""
+    fx, fy, fz = field_direction(inc_deg, dec_deg)
+
+    def closed(*b):
+        txx, tyy, tzz, txy, txz, tyz = gradient_tensor(*b)
+        return (fx * fx * txx + fy * fy * tyy + fz * fz * tzz
+                + 2.0 * (fx * fy * txy + fx * fz * txz + fy * fz * tyz))
+
+    def f(x, y, z):
+        r2 = x * x + y * y + z * z
+        fr = fx * x + fy * y + fz * z
+        return (3.0 * fr * fr - r2) / (r2 * r2 * np.sqrt(r2))
+    return field_nt / (4.0 * np.pi) * _hybrid(x1, x2, y1, y2, z1, z2, closed, f)

@@ -51,7 +51,10 @@ bool factor(int n, std::vector<int>& rad) {
 
 // Smallest-cost transform length >= nmin: cost ~ n * (passes + 1), since every pass
 // moves all n values through shared memory once and the stage loads/stores once more.
+// Length 1 would have no pass at all (the fused first/last steps run inside passes), so
+// the shortest transform is 2.
 int choose_length(int nmin) {
+  if (nmin < 2) nmin = 2;
   int best = -1;
   double best_cost = 1e300;
   std::vector<int> rad;
@@ -61,6 +64,36 @@ int choose_length(int nmin) {
     if (cost < best_cost) { best_cost = cost; best = n; }
   }
   return best;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, double* x, double* w) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n; ++i) {
+    long double z = cosl(pi * (i + 0.75L) / (n + 0.5L));
+    long double dp = 1;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1);
+      const long double dz = p1 / dp;
+      z -= dz;
+      if (fabsl(dz) < 1e-30L) break;
+    }
+    long double p0 = 1, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1);
+    x[i] = (double)z;
+    w[i] = (double)(2.0L / ((1 - z * z) * dp * dp));
+  }
 }
 
 struct HostPlan {
@@ -270,6 +303,9 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
     const double I = inc * 3.14159265358979323846 / 180.0, D = dec * 3.14159265358979323846 / 180.0;
     ta.fx = cos(I) * cos(D); ta.fy = cos(I) * sin(D); ta.fz = sin(I); ta.field = field;
     ta.out = d_tab;
+    gauss_legendre(6, ta.g6x, ta.g6w);
+    gauss_legendre(8, ta.g8x, ta.g8w);
+    gauss_legendre(14, ta.g14x, ta.g14w);
     TF_TRY(tfk::launch_table(ta, s), "kernel table launch");
 
     tfk::RowsR2C<double> ra;

@@ -54,6 +54,8 @@ struct TableArgs {
   const double* z_edges;   // device, nz+1
   double fx, fy, fz, field;  // magnetic: field direction and strength (nT)
   double* out;             // [nz][n2min][n1min]
+  // Gauss-Legendre rules for cells away from the station (see k_table)
+  double g6x[6], g6w[6], g8x[8], g8w[8], g14x[14], g14w[14];
 };
 
 struct SpecArgs {

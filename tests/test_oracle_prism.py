@@ -140,3 +140,64 @@ def test_magnetic_not_symmetric(inc, dec):
     a = prism.magnetic_dt(75.0, 125.0, -175.0, -125.0, 50.0, 100.0, inc, dec)
     b = prism.magnetic_dt(-125.0, -75.0, 125.0, 175.0, 50.0, 100.0, inc, dec)
     assert abs(a - b) > 1e-6 * abs(a)
+
+
+def _mp_exact_gravity(b):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+
+    def F(x, y, z):
+        r = mp.sqrt(x * x + y * y + z * z)
+        return x * mp.log(y + r) + y * mp.log(x + r) - z * mp.atan2(x * y, z * r)
+    s = 0
+    for i, x in enumerate(b[0:2]):
+        for j, y in enumerate(b[2:4]):
+            for k, z in enumerate(b[4:6]):
+                s += (-1) ** (i + j + k) * F(mp.mpf(x), mp.mpf(y), mp.mpf(z))
+    return float(s) * prism.GRAV_SCALE
+
+
+def _mp_exact_magnetic(b, inc, dec):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    T = [mp.mpf(0)] * 6
+    for i, x in enumerate(b[0:2]):
+        for j, y in enumerate(b[2:4]):
+            for k, z in enumerate(b[4:6]):
+                x, y, z = mp.mpf(x), mp.mpf(y), mp.mpf(z)
+                r = mp.sqrt(x * x + y * y + z * z)
+                c = -(-1) ** (i + j + k)
+                T[0] -= c * mp.atan(y * z / (x * r))
+                T[1] -= c * mp.atan(x * z / (y * r))
+                T[2] -= c * mp.atan2(x * y, z * r)
+                T[3] += c * mp.log(z + r)
+                T[4] += c * mp.log(y + r)
+                T[5] += c * mp.log(x + r)
+    fx, fy, fz = [mp.mpf(v) for v in prism.field_direction(inc, dec)]
+    q = fx * fx * T[0] + fy * fy * T[1] + fz * fz * T[2] + 2 * (fx * fy * T[3] + fx * fz * T[4]
+                                                                 + fy * fz * T[5])
+    return float(q) * prism.FIELD_NT / (4 * math.pi)
+
+
+@pytest.mark.parametrize("D", [0.5, 1.7, 1.95, 2.05, 2.6, 3.5, 4.1, 5.0, 7.9, 9.0, 40.0, 150.0])
+def test_cell_entries_accurate_at_every_distance(D):
+    # the hybrid closed-form / quadrature entries agree with 40-digit evaluations
+    worst_g = worst_m = 0.0
+    for ang in (0.1, 0.7, 1.3):
+        for zc in (25.0, 125.0):
+            cx = D * 50 * math.cos(ang) + 12.5
+            cy = D * 50 * math.sin(ang) * 0.7 - 12.5
+            b = (cx - 25, cx + 25, cy - 25, cy + 25, zc - 25, zc + 25)
+            eg = _mp_exact_gravity(b)
+            em = _mp_exact_magnetic(b, 50.0, 10.0)
+            worst_g = max(worst_g, abs(prism.gravity_cell(*b) - eg) / abs(eg))
+            worst_m = max(worst_m, abs(prism.magnetic_cell(*b, 50.0, 10.0) - em) / abs(em))
+    assert worst_g < 2e-13 and worst_m < 2e-13, (worst_g, worst_m)
+
+
+def test_closed_form_loses_digits_far_away():
+    # documents why far entries use quadrature: 150 cells away the corner sum is poor
+    b = (7475.0, 7525.0, -2275.0, -2225.0, 0.0, 50.0)
+    eg = _mp_exact_gravity(b)
+    assert abs(prism.gravity_gz(*b) - eg) / eg > 1e-9
+    assert abs(prism.gravity_cell(*b) - eg) / eg < 1e-14
