@@ -139,6 +139,26 @@ tf_status tf_get_tuning(const tf_op* op, int* rows_tile, int* cols_tile, int64_t
 tf_status tf_profile_enable(tf_op* op, int enable);
 tf_status tf_profile_read(tf_op* op, double* ms, int64_t* launches, int64_t* columns);
 
+/* d = diag(rowscale) G diag(colscale) x for one column, like tf_matvec, but without
+ * allocating anything.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc when they run the product -- for example code
+ * running under a memory budget that forbids new device allocations, or between
+ * points where an allocator must not be entered.  The operator itself must have been
+ * created beforehand (creation allocates).  Instead of the operator's workspace the
+ * call uses a fixed 8 MiB scratch buffer compiled into the library (a __device__ array
+ * that every GPU loading the library holds until the process exits).
+ *  - The first call on a device looks up the buffer's address there; make that first
+ *    call before any stream capture.  The current device must be the operator's.
+ *  - All calls share the one buffer, which keeps the previous call's contents (every
+ *    value the product reads from it is written first in the same call).  Calls that
+ *    overlap on the GPU -- on different streams, or from different host threads without
+ *    ordering -- race on the buffer and give wrong results.
+ *  - Errors: TF_EINVAL if the operator needs more than 8 MiB of scratch for one column
+ *    (nz*ny*(n1/2+1) + sy*(n1/2+1) complex values of its dtype, plus alignment), if x or
+ *    d is NULL, or if another device is current; TF_ECUDA if a launch fails. */
+tf_status tf_matvec_noalloc(const tf_op* op, const void* x, void* d, const void* colscale,
+                            const void* rowscale, tf_stream stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* tf_last_error(void);
 

@@ -54,6 +54,7 @@ SIGNATURES = {
     "tf_get_tuning": [vp, P(c_int), P(c_int), P(i64)],
     "tf_profile_enable": [vp, c_int],
     "tf_profile_read": [vp, P(ctypes.c_double), P(i64), P(i64)],
+    "tf_matvec_noalloc": [vp, vp, vp, vp, vp, vp],
 }
 
 

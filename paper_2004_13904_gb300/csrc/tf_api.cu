@@ -6,6 +6,7 @@
 
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -576,3 +577,92 @@ tf_status tf_profile_read(tf_op* op, double* ms, int64_t* launches, int64_t* col
 const char* tf_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+// ---- forward product without any allocation --------------------------------------------
+//
+// tf_matvec_noalloc runs the same three product stages as tf_matvec for one column, but
+// takes its scratch (the row-transformed layers and the column-stage output) from a
+// fixed buffer compiled into this library instead of the operator's workspace.  The
+// buffer is a file-scope __device__ array, so every GPU that loads the library holds
+// kNoallocScratchBytes of it until the process exits.  Host code cannot use the array's
+// name as a device address; its address is looked up once per device with
+// cudaGetSymbolAddress (on the first call on that device) and cached.
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename T>
+tf_status noalloc_forward(const tf_op* op, const T* x, T* d, const T* cs, const T* rs,
+                          void* scratch, cudaStream_t s) {
+  typedef typename CT<T>::C C;
+  C* w1 = (C*)scratch;
+  C* w2 = (C*)((unsigned char*)scratch + round256(op->w1_per_col() * op->csize()));
+  const C* tw1 = (const C*)op->tw1;
+  const C* tw2 = (const C*)op->tw2;
+  tfk::RowsR2C<T> a;
+  a.src = x; a.src_ld = op->n(); a.row_len = op->nx; a.nrows = op->nz * op->ny;
+  a.seq_off = 0; a.scale = cs; a.dst = w1; a.dst_ld = op->w1_per_col(); a.nh = op->nh;
+  a.plan = op->p1.plan; a.tw = tw1;
+  cudaError_t e = tfk::launch_rows_r2c<T>(a, 1, op->rows_tile, s);
+  if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
+  tfk::ColsFwd<T> b;
+  b.z = w1; b.z_ld = op->w1_per_col(); b.spec = (const C*)op->spec; b.s = w2;
+  b.s_ld = op->w2_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
+  b.plan = op->p2.plan; b.tw = tw2;
+  e = tfk::launch_cols_fwd<T>(b, 1, op->cols_tile, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cols_fwd launch");
+  tfk::RowsC2R<T> c;
+  c.src = w2; c.src_ld = op->w2_per_col(); c.nh = op->nh; c.nrows = op->sy;
+  c.dst = d; c.dst_ld = op->m(); c.out_len = op->sx; c.seq_off = op->nx - 1;
+  c.scale = rs; c.plan = op->p1.plan; c.tw = tw1;
+  e = tfk::launch_rows_c2r<T>(c, 1, op->rows_tile, s);
+  if (e != cudaSuccess) return cuda_fail(e, "rows_c2r launch");
+  return TF_OK;
+}
+
+}  // namespace
+
+extern "C" tf_status tf_matvec_noalloc(const tf_op* op, const void* x, void* d,
+                                       const void* colscale, const void* rowscale,
+                                       tf_stream stream) {
+  if (check_op(op)) return TF_EINVAL;
+  if (!x || !d) return fail(TF_EINVAL, "x and d must be non-NULL");
+  const size_t need = round256(op->w1_per_col() * op->csize()) + op->w2_per_col() * op->csize();
+  if (need > kNoallocScratchBytes)
+    return fail(TF_EINVAL,
+                "tf_matvec_noalloc: this operator needs %zu bytes of scratch per column, more "
+                "than the library's fixed %zu-byte buffer; use tf_matvec",
+                need, kNoallocScratchBytes);
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != op->device)
+    return fail(TF_EINVAL, "current device %d is not the operator's device %d", dev, op->device);
+  if (dev < 0 || dev >= kNoallocMaxDevices)
+    return fail(TF_EUNSUPPORTED, "device index %d above %d", dev, kNoallocMaxDevices - 1);
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+      g_noalloc_ptr[dev] = p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (op->dtype == TF_F32)
+    return noalloc_forward<float>(op, (const float*)x, (float*)d, (const float*)colscale,
+                                  (const float*)rowscale, scratch, s);
+  return noalloc_forward<double>(op, (const double*)x, (double*)d, (const double*)colscale,
+                                 (const double*)rowscale, scratch, s);
+}
