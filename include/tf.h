@@ -122,12 +122,24 @@ tf_status tf_rmatmat(tf_op* op, int64_t B, const void* Y, int64_t ldy, void* X, 
  * memory; bytes must equal that size).  Ordered on stream.  For checks and tools. */
 tf_status tf_get_spectra(const tf_op* op, void* dst, int64_t bytes, tf_stream stream);
 
-/* Tuning knobs of the product kernels: rows-stage sequence pairs per CTA (4, 8, 16),
- * column-stage k1 columns per CTA (4, 8, 16), and columns per workspace chunk (>= 1;
- * the workspace is reallocated to fit).  0 keeps the current value.  Must not be
- * called while products of this operator are in flight. */
+/* Tuning knobs of the product kernels: rows-stage sequence pairs per CTA (4, 8, 16) and
+ * column-stage k1 columns per CTA (4, 8, 16) of the generic engine (the compile-time
+ * plans have fixed tiles), and columns per workspace chunk (>= 1; the workspace is
+ * reallocated to exactly that many columns and no longer grows).  0 keeps the current
+ * value.  By default the workspace grows, on the first product with more columns than
+ * it holds, up to the columns that fit in 2 GiB (the growth frees and allocates device
+ * memory, which waits for the device to be idle).  Must not be called while products of
+ * this operator are in flight. */
 tf_status tf_set_tuning(tf_op* op, int rows_tile, int cols_tile, int64_t chunk_cols);
 tf_status tf_get_tuning(const tf_op* op, int* rows_tile, int* cols_tile, int64_t* chunk_cols);
+
+/* FFT engine of the product kernels: 0 (default) uses compile-time plans for the
+ * transform lengths that have one (32, 64, 96, 128, 160, 192, 224, 256, 320, 448, 512)
+ * and the generic engine otherwise; 1 forces the generic engine.  Both compute the same
+ * product.  tf_get_engine also reports whether the row (x) and column (y) transforms
+ * currently run on compiled plans. */
+tf_status tf_set_engine(tf_op* op, int engine);
+tf_status tf_get_engine(const tf_op* op, int* engine, int* compiled_rows, int* compiled_cols);
 
 /* Per-stage timing with CUDA events recorded around every stage launch on the call's
  * stream.  Enable (1) / disable (0) clears the record.  tf_profile_read synchronises
@@ -158,6 +170,14 @@ tf_status tf_profile_read(tf_op* op, double* ms, int64_t* launches, int64_t* col
  *    d is NULL, or if another device is current; TF_ECUDA if a launch fails. */
 tf_status tf_matvec_noalloc(const tf_op* op, const void* x, void* d, const void* colscale,
                             const void* rowscale, tf_stream stream);
+
+/* Bounds checking (debug builds).  In a library compiled with -DTF_BOUNDS_CHECK
+ * (libtf_checked.so), every global access of the product kernels is tested against its
+ * buffer's extent and skipped when outside it; the first violation is recorded.  This
+ * call returns and clears that record: *checked = 1 in a checked build (else 0), *site
+ * identifies the access (0 = none recorded), *offset and *extent its element offset
+ * within the column's buffer and that buffer's length.  Synchronises the device. */
+tf_status tf_debug_oob(int* checked, int* site, int64_t* offset, int64_t* extent);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char* tf_last_error(void);

@@ -199,6 +199,16 @@ class Operator:
                                             ctypes.byref(c)))
         return a.value, b.value, c.value
 
+    def set_engine(self, engine: int):
+        """0: compile-time FFT plans where available (default); 1: generic engine."""
+        _lib.check(_lib.lib().tf_set_engine(self._h, int(engine)))
+
+    def engine(self):
+        e, r, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.check(_lib.lib().tf_get_engine(self._h, ctypes.byref(e), ctypes.byref(r),
+                                            ctypes.byref(c)))
+        return e.value, bool(r.value), bool(c.value)
+
     def profile(self, enable: bool):
         _lib.check(_lib.lib().tf_profile_enable(self._h, 1 if enable else 0))
 

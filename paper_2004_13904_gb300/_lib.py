@@ -10,7 +10,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libtf.so")
+# TF_LIB_VARIANT=checked loads the bounds-checked debug build (libtf_checked.so).
+LIB_PATH = os.path.join(HERE, "_build", "libtf_checked.so" if os.environ.get(
+    "TF_LIB_VARIANT") == "checked" else "libtf.so")
 
 TF_OK, TF_EINVAL, TF_ENOMEM, TF_ECUDA, TF_EUNSUPPORTED, TF_ENOTCONV, TF_ETIMEOUT = range(7)
 TF_F32, TF_F64 = 0, 1
@@ -55,6 +57,9 @@ SIGNATURES = {
     "tf_profile_enable": [vp, c_int],
     "tf_profile_read": [vp, P(ctypes.c_double), P(i64), P(i64)],
     "tf_matvec_noalloc": [vp, vp, vp, vp, vp, vp],
+    "tf_set_engine": [vp, c_int],
+    "tf_get_engine": [vp, P(c_int), P(c_int), P(c_int)],
+    "tf_debug_oob": [P(c_int), P(c_int), P(i64), P(i64)],
 }
 
 

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtf.so")
-SOURCES = ["tf_api.cu", "tf_kernels.cu"]
+SOURCES = ["tf_api.cu", "tf_kernels.cu", "tf_ct_f32.cu", "tf_ct_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -42,18 +42,23 @@ def _newer(target: str, deps) -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
+def build(verbose: bool = False, force: bool = False, checked: bool = False) -> str:
+    """Compile libtf.so (or, with checked=True, the bounds-checked libtf_checked.so)."""
     os.makedirs(OUT, exist_ok=True)
+    lib = os.path.join(OUT, "libtf_checked.so") if checked else LIB
+    tag = "_checked" if checked else ""
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, "..", "include", "tf.h"))
-    if not force and _newer(LIB, deps):
-        return LIB
+    if not force and _newer(lib, deps):
+        return lib
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(OUT, os.path.splitext(src)[0] + tag + ".o")
         cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose)
+        if checked:
+            cmd.append("-DTF_BOUNDS_CHECK")
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -63,14 +68,14 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, checked="--checked" in sys.argv))

@@ -50,12 +50,17 @@ bool factor(int n, std::vector<int>& rad) {
   return m == 1 && (int)rad.size() <= tfk::kMaxPass;
 }
 
-// Smallest-cost transform length >= nmin: cost ~ n * (passes + 1), since every pass
-// moves all n values through shared memory once and the stage loads/stores once more.
+// Transform length >= nmin.  Lengths with a compile-time plan run about twice as fast
+// per element as the generic engine, so the smallest of those is taken when one fits;
+// otherwise the generic length of least cost ~ n * (passes + 1), since every pass moves
+// all n values through shared memory once and the stage loads/stores once more.
 // Length 1 would have no pass at all (the fused first/last steps run inside passes), so
 // the shortest transform is 2.
-int choose_length(int nmin) {
+int choose_length(int nmin, bool use_menu) {
   if (nmin < 2) nmin = 2;
+  if (use_menu)
+    for (int i = 0; i < tfk::ct_menu_count(); ++i)
+      if (tfk::ct_menu_length(i) >= nmin) return tfk::ct_menu_length(i);
   int best = -1;
   double best_cost = 1e300;
   std::vector<int> rad;
@@ -130,6 +135,21 @@ HostPlan make_plan(int n) {
   return h;
 }
 
+// True when the compile-time menu has this length with the same radix order as the
+// host plan (so both engines share one twiddle table).
+bool has_ct_plan(const HostPlan& h) {
+  for (int i = 0; i < tfk::ct_menu_count(); ++i) {
+    if (tfk::ct_menu_length(i) != h.plan.n) continue;
+    int r[tfk::kMaxPass];
+    const int np = tfk::ct_menu_radices(i, r);
+    if (np != h.plan.np) return false;
+    for (int p = 0; p < np; ++p)
+      if (r[p] != h.plan.radix[p]) return false;
+    return true;
+  }
+  return false;
+}
+
 }  // namespace
 
 struct tf_op {
@@ -150,8 +170,11 @@ struct tf_op {
   // workspace
   void* w1 = nullptr;   // chunk * nz*ny*nh complex
   void* w2 = nullptr;   // chunk * sy*nh complex
-  int64_t chunk = 0;
+  int64_t chunk = 0;       // columns the allocated workspace holds
+  int64_t chunk_cap = 0;   // most columns per chunk (grown into on demand)
   int rows_tile = 8, cols_tile = 8;
+  bool ct1 = false, ct2 = false;  // compile-time plans exist for n1 / n2
+  int engine = 0;                 // 0: compile-time plans where available, 1: generic
   // profiling
   bool prof = false;
   struct Rec { int stage; int64_t cols; cudaEvent_t a, b; };
@@ -195,27 +218,40 @@ tf_status upload_twiddles(const HostPlan& h, tf_dtype dt, void** dst) {
   return e == cudaSuccess ? TF_OK : cuda_fail(e, "cudaMemcpy(twiddles)");
 }
 
+// Each workspace buffer carries a guard tail of one full transform column block
+// (n2 * nh complex values) beyond the last column it serves, so that no read near the
+// end of a column block can leave the allocation.
 tf_status alloc_workspace(tf_op* op, int64_t chunk) {
   cudaFree(op->w1);
   cudaFree(op->w2);
   op->w1 = op->w2 = nullptr;
   op->chunk = 0;
-  cudaError_t e = cudaMalloc(&op->w1, (size_t)chunk * op->w1_per_col() * op->csize());
+  const size_t guard = (size_t)op->n2 * op->nh * op->csize();
+  cudaError_t e = cudaMalloc(&op->w1, (size_t)chunk * op->w1_per_col() * op->csize() + guard);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
-  e = cudaMalloc(&op->w2, (size_t)chunk * op->w2_per_col() * op->csize());
+  e = cudaMalloc(&op->w2, (size_t)chunk * op->w2_per_col() * op->csize() + guard);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
   op->chunk = chunk;
   return TF_OK;
 }
 
-// Default chunk: keep the per-chunk intermediate (the row-transformed model block) near
-// 48 MB so that it stays resident in the 126 MB L2 between the row and column stages.
-int64_t default_chunk(const tf_op* op) {
-  const double per = (double)op->w1_per_col() * op->csize();
-  int64_t c = (int64_t)(48.0e6 / per);
+// Most columns per chunk: a 2 GiB workspace budget.  Measured on the c2 block, one
+// chunk of 1260 columns ran 20 % faster than L2-sized chunks of 48: the column stage
+// needs many CTAs per launch more than it needs its input resident in L2.
+int64_t default_chunk_cap(const tf_op* op) {
+  const double per = (double)(op->w1_per_col() + op->w2_per_col()) * op->csize();
+  int64_t c = (int64_t)(2147483648.0 / per);
   if (c < 1) c = 1;
   if (c > 4096) c = 4096;
   return c;
+}
+
+// Grows the workspace (once, stream-ordered through cudaFree's implicit
+// synchronisation) so that a block of B columns runs in as few chunks as the cap allows.
+tf_status ensure_workspace(tf_op* op, int64_t B) {
+  const int64_t want = std::min<int64_t>(B, op->chunk_cap);
+  if (op->chunk >= want) return TF_OK;
+  return alloc_workspace(op, want);
 }
 
 tf_status create_common(const tf_grid* g, int kind, double inc, double dec, double field,
@@ -249,8 +285,8 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
   cudaGetDevice(&op->device);
 
   const int n1min = op->sx + op->nx - 1, n2min = op->sy + op->ny - 1;
-  op->n1 = choose_length(n1min);
-  op->n2 = choose_length(n2min);
+  op->n1 = choose_length(n1min, true);
+  op->n2 = choose_length(n2min, true);
   if (op->n1 < 0 || op->n2 < 0 || op->n1 > kMaxFft || op->n2 > kMaxFft) {
     delete op;
     return fail(TF_EUNSUPPORTED, "embedding %d x %d exceeds the supported %d per axis", n1min,
@@ -259,6 +295,8 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
   op->nh = op->n1 / 2 + 1;
   op->p1 = make_plan(op->n1);
   op->p2 = make_plan(op->n2);
+  op->ct1 = has_ct_plan(op->p1);
+  op->ct2 = has_ct_plan(op->p2);
   op->rows_tile = dt == TF_F32 ? 8 : 4;
   op->cols_tile = dt == TF_F32 ? 8 : 4;
 
@@ -329,7 +367,8 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
     TF_TRY(tfk::launch_to_f32(d_spec64, (float2*)op->spec, nspec, s), "spectra rounding");
   }
   TF_TRY(cudaStreamSynchronize(s), "spectra set-up");
-  if ((st = alloc_workspace(op, default_chunk(op))) != TF_OK) goto done;
+  op->chunk_cap = default_chunk_cap(op);
+  if ((st = alloc_workspace(op, 1)) != TF_OK) goto done;
 
 done:
 #undef TF_TRY
@@ -371,6 +410,8 @@ template <typename T>
 tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int64_t ldd,
                        const T* cs, const T* rs, cudaStream_t s) {
   typedef typename CT<T>::C C;
+  tf_status st = ensure_workspace(op, B);
+  if (st != TF_OK) return st;
   C* w1 = (C*)op->w1;
   C* w2 = (C*)op->w2;
   const C* tw1 = (const C*)op->tw1;
@@ -381,19 +422,26 @@ tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int6
     a.src = X + c0 * ldx; a.src_ld = ldx; a.row_len = op->nx; a.nrows = op->nz * op->ny;
     a.seq_off = 0; a.scale = cs; a.dst = w1; a.dst_ld = op->w1_per_col(); a.nh = op->nh;
     a.plan = op->p1.plan; a.tw = tw1;
-    cudaError_t e = stage(op, 0, cb, s, [&] { return tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s); });
+    const bool c1 = op->engine == 0 && op->ct1, c2 = op->engine == 0 && op->ct2;
+    cudaError_t e = stage(op, 0, cb, s, [&] {
+      return c1 ? tfk::ct_rows_r2c<T>(a, cb, s) : tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
     tfk::ColsFwd<T> b;
     b.z = w1; b.z_ld = op->w1_per_col(); b.spec = (const C*)op->spec; b.s = w2;
     b.s_ld = op->w2_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
     b.plan = op->p2.plan; b.tw = tw2;
-    e = stage(op, 1, cb, s, [&] { return tfk::launch_cols_fwd<T>(b, cb, op->cols_tile, s); });
+    e = stage(op, 1, cb, s, [&] {
+      return c2 ? tfk::ct_cols_fwd<T>(b, cb, s) : tfk::launch_cols_fwd<T>(b, cb, op->cols_tile, s);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "cols_fwd launch");
     tfk::RowsC2R<T> c;
     c.src = w2; c.src_ld = op->w2_per_col(); c.nh = op->nh; c.nrows = op->sy;
     c.dst = D + c0 * ldd; c.dst_ld = ldd; c.out_len = op->sx; c.seq_off = op->nx - 1;
     c.scale = rs; c.plan = op->p1.plan; c.tw = tw1;
-    e = stage(op, 2, cb, s, [&] { return tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s); });
+    e = stage(op, 2, cb, s, [&] {
+      return c1 ? tfk::ct_rows_c2r<T>(c, cb, s) : tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "rows_c2r launch");
   }
   return TF_OK;
@@ -403,6 +451,8 @@ template <typename T>
 tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int64_t ldx,
                        const T* cs, const T* rs, cudaStream_t s) {
   typedef typename CT<T>::C C;
+  tf_status st = ensure_workspace(op, B);
+  if (st != TF_OK) return st;
   C* w1 = (C*)op->w1;
   C* w2 = (C*)op->w2;
   const C* tw1 = (const C*)op->tw1;
@@ -413,19 +463,26 @@ tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int6
     a.src = Y + c0 * ldy; a.src_ld = ldy; a.row_len = op->sx; a.nrows = op->sy;
     a.seq_off = op->nx - 1; a.scale = rs; a.dst = w2; a.dst_ld = op->w2_per_col();
     a.nh = op->nh; a.plan = op->p1.plan; a.tw = tw1;
-    cudaError_t e = stage(op, 3, cb, s, [&] { return tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s); });
+    const bool c1 = op->engine == 0 && op->ct1, c2 = op->engine == 0 && op->ct2;
+    cudaError_t e = stage(op, 3, cb, s, [&] {
+      return c1 ? tfk::ct_rows_r2c<T>(a, cb, s) : tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
     tfk::ColsAdj<T> b;
     b.z = w2; b.z_ld = op->w2_per_col(); b.spec = (const C*)op->spec; b.u = w1;
     b.u_ld = op->w1_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
     b.plan = op->p2.plan; b.tw = tw2;
-    e = stage(op, 4, cb, s, [&] { return tfk::launch_cols_adj<T>(b, cb, op->cols_tile, s); });
+    e = stage(op, 4, cb, s, [&] {
+      return c2 ? tfk::ct_cols_adj<T>(b, cb, s) : tfk::launch_cols_adj<T>(b, cb, op->cols_tile, s);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "cols_adj launch");
     tfk::RowsC2R<T> c;
     c.src = w1; c.src_ld = op->w1_per_col(); c.nh = op->nh; c.nrows = op->nz * op->ny;
     c.dst = X + c0 * ldx; c.dst_ld = ldx; c.out_len = op->nx; c.seq_off = 0; c.scale = cs;
     c.plan = op->p1.plan; c.tw = tw1;
-    e = stage(op, 5, cb, s, [&] { return tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s); });
+    e = stage(op, 5, cb, s, [&] {
+      return c1 ? tfk::ct_rows_c2r<T>(c, cb, s) : tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "rows_c2r launch");
   }
   return TF_OK;
@@ -534,10 +591,28 @@ tf_status tf_set_tuning(tf_op* op, int rows_tile, int cols_tile, int64_t chunk_c
     return fail(TF_EUNSUPPORTED, "tile needs more than 227 KB of shared memory");
   op->rows_tile = rt;
   op->cols_tile = ct;
-  if (chunk_cols && chunk_cols != op->chunk) {
-    cudaDeviceSynchronize();
-    return alloc_workspace(op, chunk_cols);
+  if (chunk_cols) {
+    op->chunk_cap = chunk_cols;
+    if (chunk_cols != op->chunk) {
+      cudaDeviceSynchronize();
+      return alloc_workspace(op, chunk_cols);
+    }
   }
+  return TF_OK;
+}
+
+tf_status tf_set_engine(tf_op* op, int engine) {
+  if (check_op(op)) return TF_EINVAL;
+  if (engine != 0 && engine != 1) return fail(TF_EINVAL, "engine must be 0 or 1");
+  op->engine = engine;
+  return TF_OK;
+}
+
+tf_status tf_get_engine(const tf_op* op, int* engine, int* compiled_rows, int* compiled_cols) {
+  if (check_op(op)) return TF_EINVAL;
+  if (engine) *engine = op->engine;
+  if (compiled_rows) *compiled_rows = op->engine == 0 && op->ct1;
+  if (compiled_cols) *compiled_cols = op->engine == 0 && op->ct2;
   return TF_OK;
 }
 
@@ -571,6 +646,25 @@ tf_status tf_profile_read(tf_op* op, double* ms, int64_t* launches, int64_t* col
     launches[r.stage] += 1;
     columns[r.stage] += r.cols;
   }
+  return TF_OK;
+}
+
+tf_status tf_debug_oob(int* checked, int* site, int64_t* offset, int64_t* extent) {
+  tfk::OobRecord recs[3];
+  bool ok = tfk::oob_read_generic(&recs[0], true);
+  ok = tfk::oob_read_ct_f32(&recs[1], true) && ok;
+  ok = tfk::oob_read_ct_f64(&recs[2], true) && ok;
+  if (checked) *checked = ok ? 1 : 0;
+  if (site) *site = 0;
+  if (offset) *offset = 0;
+  if (extent) *extent = 0;
+  for (auto& r : recs)
+    if (r.hit) {
+      if (site) *site = r.site;
+      if (offset) *offset = r.off;
+      if (extent) *extent = r.ext;
+      break;
+    }
   return TF_OK;
 }
 

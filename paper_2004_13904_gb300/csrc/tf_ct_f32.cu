@@ -1,0 +1,22 @@
+// Compile-time-plan product kernels, float instantiations (see tf_ct_kernels.cuh).
+#include "tf_ct_kernels.cuh"
+
+namespace tfk {
+TF_DEFINE_OOB_READER(oob_read_ct_f32)
+TF_CT_DEFINE_DISPATCH(float)
+
+namespace {
+struct MenuEntry { int n; int np; int r[4]; };
+template <int... R> constexpr int count_of() { return (int)sizeof...(R); }
+#define TF_CT_MENU_ENTRY(N, ...) {N, count_of<__VA_ARGS__>(), {__VA_ARGS__}},
+const MenuEntry kMenu[] = {TF_CT_MENU(TF_CT_MENU_ENTRY)};
+#undef TF_CT_MENU_ENTRY
+}  // namespace
+
+int ct_menu_count() { return (int)(sizeof(kMenu) / sizeof(kMenu[0])); }
+int ct_menu_length(int i) { return kMenu[i].n; }
+int ct_menu_radices(int i, int* radices) {
+  for (int p = 0; p < kMenu[i].np; ++p) radices[p] = kMenu[i].r[p];
+  return kMenu[i].np;
+}
+}  // namespace tfk

@@ -1,0 +1,7 @@
+// Compile-time-plan product kernels, double instantiations (see tf_ct_kernels.cuh).
+#include "tf_ct_kernels.cuh"
+
+namespace tfk {
+TF_DEFINE_OOB_READER(oob_read_ct_f64)
+TF_CT_DEFINE_DISPATCH(double)
+}  // namespace tfk

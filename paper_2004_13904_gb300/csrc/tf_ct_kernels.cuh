@@ -1,0 +1,352 @@
+// Product kernels on the compile-time FFT engine (tf_fft_ct.cuh), for the transform
+// lengths of TF_CT_MENU.  They compute exactly what the generic kernels of
+// tf_kernels.cu compute (same stages, same data layout, same twiddle tables); only the
+// index arithmetic is resolved at compile time.  Included by tf_ct_f32.cu / tf_ct_f64.cu.
+#pragma once
+#include "tf_check.cuh"
+#include "tf_fft_ct.cuh"
+#include "tf_internal.h"
+
+// Transform lengths with a compile-time plan, and their radix lists (the same order
+// the host planner produces: eights first, then a four or two, then 7, 5, 3).
+#define TF_CT_MENU(X)        \
+  X(32, 8, 4)                \
+  X(64, 8, 8)                \
+  X(96, 8, 4, 3)             \
+  X(128, 8, 8, 2)            \
+  X(160, 8, 4, 5)            \
+  X(192, 8, 8, 3)            \
+  X(224, 8, 4, 7)            \
+  X(256, 8, 8, 4)            \
+  X(320, 8, 8, 5)            \
+  X(448, 8, 8, 7)            \
+  X(512, 8, 8, 8)
+
+namespace tfk {
+namespace ctk {
+
+using ct::Vec;
+
+__host__ __device__ constexpr int twpad(int c) { return (c + 1) & ~1; }
+
+template <typename C> __device__ __forceinline__ C zero() { return mk<C>(0, 0); }
+
+template <typename T, class P, int TB, int V, int NT>
+__global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
+  typedef typename CT<T>::C C;
+  constexpr int N = P::n, NH = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + twpad(N - 1);
+  for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  const int pair0 = blockIdx.x * TB;
+  const T* src = a.src + (int64_t)blockIdx.y * a.src_ld;
+  const int len = a.row_len, off = a.seq_off, nrows = a.nrows;
+  const int src_ext = nrows * len;
+  const T* scale = a.scale;
+  for (int u = threadIdx.x; u < TB * N; u += NT) {
+    const int pp = u / N, n = u - pp * N;
+    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+    const int e = n - off;
+    T xa = T(0), xb = T(0);
+    if (e >= 0 && e < len) {
+      if (ra < nrows) {
+        const int o = ra * len + e;
+        if (TF_IN(kSiteR2cSrc, o, src_ext)) xa = src[o];
+        if (scale && TF_IN(kSiteR2cScale, o, src_ext)) xa *= scale[o];
+      }
+      if (rb < nrows) {
+        const int o = rb * len + e;
+        if (TF_IN(kSiteR2cSrc, o, src_ext)) xb = src[o];
+        if (scale && TF_IN(kSiteR2cScale, o, src_ext)) xb *= scale[o];
+      }
+    }
+    buf[ct::at<C, TB>(n, pp)] = mk<C>(xa, xb);
+  }
+  __syncthreads();
+  const ct::Buf<C, TB, V> b{buf, N * TB};
+  P::template run<TB, V, NT, false>(tw, buf, b, b);
+  C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
+  const int dst_ext = nrows * NH;
+  for (int u = threadIdx.x; u < TB * NH; u += NT) {
+    const int pp = u / NH, k = u - pp * NH;
+    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+    if (ra >= nrows) continue;
+    const C z = buf[ct::at<C, TB>(k, pp)];
+    C zc = buf[ct::at<C, TB>(k ? N - k : 0, pp)];
+    zc.y = -zc.y;
+    if (TF_IN(kSiteR2cDst, ra * NH + k, dst_ext))
+      dst[ra * NH + k] = mk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
+    if (rb < nrows && TF_IN(kSiteR2cDst, rb * NH + k, dst_ext))
+      dst[rb * NH + k] = mk<C>(T(0.5) * (z.y - zc.y), T(-0.5) * (z.x - zc.x));
+  }
+}
+
+template <typename T, class P, int TB, int V, int NT>
+__global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
+  typedef typename CT<T>::C C;
+  constexpr int N = P::n, NH = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + twpad(N - 1);
+  for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  const int pair0 = blockIdx.x * TB;
+  const int nrows = a.nrows;
+  const C* src = a.src + (int64_t)blockIdx.y * a.src_ld;
+  const int src_ext = nrows * NH;
+  for (int u = threadIdx.x; u < TB * NH; u += NT) {
+    const int pp = u / NH, k = u - pp * NH;
+    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+    C xa = zero<C>(), xb = zero<C>();
+    if (ra < nrows && TF_IN(kSiteC2rSrc, ra * NH + k, src_ext)) xa = src[ra * NH + k];
+    if (rb < nrows && TF_IN(kSiteC2rSrc, rb * NH + k, src_ext)) xb = src[rb * NH + k];
+    const bool self = (k == 0) || (2 * k == N);
+    if (self) { xa.y = T(0); xb.y = T(0); }
+    buf[ct::at<C, TB>(k, pp)] = mk<C>(xa.x - xb.y, xa.y + xb.x);
+    if (!self) buf[ct::at<C, TB>(N - k, pp)] = mk<C>(xa.x + xb.y, xb.x - xa.y);
+  }
+  __syncthreads();
+  const ct::Buf<C, TB, V> b{buf, N * TB};
+  P::template run<TB, V, NT, true>(tw, buf, b, b);
+  T* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
+  const int L = a.out_len, off = a.seq_off;
+  const int dst_ext = nrows * L;
+  const T* scale = a.scale;
+  for (int u = threadIdx.x; u < TB * L; u += NT) {
+    const int pp = u / L, i = u - pp * L;
+    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+    if (ra >= nrows) continue;
+    const C z = buf[ct::at<C, TB>(off + i, pp)];
+    const int oa = ra * L + i;
+    if (TF_IN(kSiteC2rDst, oa, dst_ext))
+      dst[oa] = (scale && TF_IN(kSiteC2rScale, oa, dst_ext)) ? z.x * scale[oa] : z.x;
+    if (rb < nrows) {
+      const int ob = rb * L + i;
+      if (TF_IN(kSiteC2rDst, ob, dst_ext))
+        dst[ob] = (scale && TF_IN(kSiteC2rScale, ob, dst_ext)) ? z.y * scale[ob] : z.y;
+    }
+  }
+}
+
+template <typename T, class P, int TB, int V, int NT>
+__global__ void __launch_bounds__(NT) k_cols_fwd(const ColsFwd<T> a) {
+  typedef typename CT<T>::C C;
+  constexpr int N = P::n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + twpad(N - 1);
+  C* acc = buf + N * TB;
+  for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  __syncthreads();
+  const int k0 = blockIdx.x * TB;
+  const int nh = a.nh, ny = a.ny, sy = a.sy;
+  const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
+  const int z_ext = a.nz * ny * nh, g_ext = a.nz * N * nh, s_ext = sy * nh;
+  const C* spec = a.spec;
+  for (int r = 0; r < a.nz; ++r) {
+    const int zoff = r * ny * nh, goff = r * N * nh;
+    const bool first_layer = (r == 0);
+    auto load = [=](int idx, int b0, C* o) {
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const int k1 = k0 + b0 + q;
+        const int e = zoff + idx * nh + k1;
+        o[q] = zero<C>();
+        if (idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e, z_ext)) o[q] = z[e];
+      }
+    };
+    auto mac = [=](int idx, int b0, const C* v, int) {
+      C cur[V];
+      const bool acc_ok = TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB);
+      if (!first_layer && acc_ok) Vec<V, C>::ld(acc + idx * TB + b0, cur);
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const int k1 = k0 + b0 + q;
+        const int e = goff + idx * nh + k1;
+        C g = zero<C>();
+        if (k1 < nh && TF_IN(kSiteFwdSpec, e, g_ext)) g = spec[e];
+        const C p = cmul(g, v[q]);
+        cur[q] = first_layer ? p : cadd(cur[q], p);
+      }
+      if (acc_ok) Vec<V, C>::st(acc + idx * TB + b0, cur);
+    };
+    P::template run<TB, V, NT, false>(tw, buf, load, mac);
+  }
+  C* s = a.s + (int64_t)blockIdx.y * a.s_ld;
+  auto lacc = [=](int idx, int b0, C* o) {
+    if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::ld(acc + idx * TB + b0, o);
+  };
+  auto store = [=](int idx, int b0, const C* v, int) {
+    const int j = idx - (ny - 1);
+    if (j < 0 || j >= sy) return;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const int k1 = k0 + b0 + q;
+      if (k1 < nh && TF_IN(kSiteFwdS, j * nh + k1, s_ext)) s[j * nh + k1] = v[q];
+    }
+  };
+  P::template run<TB, V, NT, true>(tw, buf, lacc, store);
+}
+
+template <typename T, class P, int TB, int V, int NT>
+__global__ void __launch_bounds__(NT) k_cols_adj(const ColsAdj<T> a) {
+  typedef typename CT<T>::C C;
+  constexpr int N = P::n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + twpad(N - 1);
+  C* acc = buf + N * TB;
+  for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  __syncthreads();
+  const int k0 = blockIdx.x * TB;
+  const int nh = a.nh, ny = a.ny, sy = a.sy;
+  const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
+  const int z_ext = sy * nh, g_ext = a.nz * N * nh, u_ext = a.nz * ny * nh;
+  const C* spec = a.spec;
+  auto load = [=](int idx, int b0, C* o) {
+    const int j = idx - (ny - 1);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const int k1 = k0 + b0 + q;
+      o[q] = zero<C>();
+      if (j >= 0 && j < sy && k1 < nh && TF_IN(kSiteAdjZ, j * nh + k1, z_ext)) o[q] = z[j * nh + k1];
+    }
+  };
+  auto sacc = [=](int idx, int b0, const C* v, int) {
+    if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::st(acc + idx * TB + b0, v);
+  };
+  P::template run<TB, V, NT, false>(tw, buf, load, sacc);
+  C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
+  for (int r = 0; r < a.nz; ++r) {
+    const int goff = r * N * nh, uoff = r * ny * nh;
+    auto prod = [=](int idx, int b0, C* o) {
+      C cur[V];
+      if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::ld(acc + idx * TB + b0, cur);
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const int k1 = k0 + b0 + q;
+        const int e = goff + idx * nh + k1;
+        o[q] = zero<C>();
+        if (k1 < nh && TF_IN(kSiteAdjSpec, e, g_ext)) o[q] = cmulc(cur[q], spec[e]);
+      }
+    };
+    auto store = [=](int idx, int b0, const C* v, int) {
+      if (idx >= ny) return;
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const int k1 = k0 + b0 + q;
+        const int e = uoff + idx * nh + k1;
+        if (k1 < nh && TF_IN(kSiteAdjU, e, u_ext)) u[e] = v[q];
+      }
+    };
+    P::template run<TB, V, NT, true>(tw, buf, prod, store);
+  }
+}
+
+// Dynamic shared memory above 48 KB needs an opt-in.
+template <class K> inline cudaError_t set_smem(K kernel, size_t smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Tiles: sequences per CTA (TB), sequences per thread (V), threads (NT).
+template <typename T, int N> struct Tiles;
+// Threads per CTA grow with N so that every pass needs about one butterfly task per
+// thread (no second, mostly idle iteration holding registers).
+template <int N> struct Tiles<float, N> {
+  static constexpr int TB = N <= 96 ? 16 : 8, V = 2;
+  static constexpr int NT = N <= 64 ? 64 : (N <= 256 ? 128 : 256);
+};
+template <int N> struct Tiles<double, N> {
+  static constexpr int TB = N <= 96 ? 8 : 4, V = 2, NT = 64;
+};
+
+template <typename T, class P>
+cudaError_t rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
+  typedef Tiles<T, P::n> TL;
+  auto k = k_rows_r2c<T, P, TL::TB, TL::V, TL::NT>;
+  const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB) * sizeof(typename CT<T>::C);
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(cdiv((a.nrows + 1) / 2, TL::TB), ncols), TL::NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, class P>
+cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
+  typedef Tiles<T, P::n> TL;
+  auto k = k_rows_c2r<T, P, TL::TB, TL::V, TL::NT>;
+  const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB) * sizeof(typename CT<T>::C);
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(cdiv((a.nrows + 1) / 2, TL::TB), ncols), TL::NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, class P>
+cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
+  typedef Tiles<T, P::n> TL;
+  auto k = k_cols_fwd<T, P, TL::TB, TL::V, TL::NT>;
+  const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(cdiv(a.nh, TL::TB), ncols), TL::NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, class P>
+cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
+  typedef Tiles<T, P::n> TL;
+  auto k = k_cols_adj<T, P, TL::TB, TL::V, TL::NT>;
+  const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(cdiv(a.nh, TL::TB), ncols), TL::NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ctk
+
+#define TF_CT_CASE(FN, ...) \
+  case TF_CT_FIRST(__VA_ARGS__): return ctk::FN<T, ct::Plan<__VA_ARGS__>>(a, ncols, s);
+#define TF_CT_FIRST(x, ...) x
+
+// Defines the dtype's four dispatchers: cudaErrorNotSupported for lengths off the menu.
+#define TF_CT_DEFINE_DISPATCH(TYPE)                                                        \
+  template <>                                                                              \
+  cudaError_t ct_rows_r2c<TYPE>(const RowsR2C<TYPE>& a, int ncols, cudaStream_t s) {       \
+    typedef TYPE T;                                                                        \
+    switch (a.plan.n) {                                                                    \
+      TF_CT_MENU(TF_CT_R2C_CASE)                                                           \
+      default: return cudaErrorNotSupported;                                               \
+    }                                                                                      \
+  }                                                                                        \
+  template <>                                                                              \
+  cudaError_t ct_rows_c2r<TYPE>(const RowsC2R<TYPE>& a, int ncols, cudaStream_t s) {       \
+    typedef TYPE T;                                                                        \
+    switch (a.plan.n) {                                                                    \
+      TF_CT_MENU(TF_CT_C2R_CASE)                                                           \
+      default: return cudaErrorNotSupported;                                               \
+    }                                                                                      \
+  }                                                                                        \
+  template <>                                                                              \
+  cudaError_t ct_cols_fwd<TYPE>(const ColsFwd<TYPE>& a, int ncols, cudaStream_t s) {       \
+    typedef TYPE T;                                                                        \
+    switch (a.plan.n) {                                                                    \
+      TF_CT_MENU(TF_CT_FWD_CASE)                                                           \
+      default: return cudaErrorNotSupported;                                               \
+    }                                                                                      \
+  }                                                                                        \
+  template <>                                                                              \
+  cudaError_t ct_cols_adj<TYPE>(const ColsAdj<TYPE>& a, int ncols, cudaStream_t s) {       \
+    typedef TYPE T;                                                                        \
+    switch (a.plan.n) {                                                                    \
+      TF_CT_MENU(TF_CT_ADJ_CASE)                                                           \
+      default: return cudaErrorNotSupported;                                               \
+    }                                                                                      \
+  }
+
+#define TF_CT_R2C_CASE(...) TF_CT_CASE(rows_r2c, __VA_ARGS__)
+#define TF_CT_C2R_CASE(...) TF_CT_CASE(rows_c2r, __VA_ARGS__)
+#define TF_CT_FWD_CASE(...) TF_CT_CASE(cols_fwd, __VA_ARGS__)
+#define TF_CT_ADJ_CASE(...) TF_CT_CASE(cols_adj, __VA_ARGS__)
+
+}  // namespace tfk

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tf_check.cuh"
+
 namespace tfk {
 
 template <typename T> struct CT;
@@ -195,12 +197,18 @@ __device__ __forceinline__ void fft_pass_any(int R, int nb, int Ns, int tbs, con
 }
 
 template <typename C> struct SmemLoad {
-  const C* p; int ld;
-  __device__ __forceinline__ C operator()(int idx, int b) const { return p[idx * ld + b]; }
+  const C* p; int ld; int ext;
+  __device__ __forceinline__ C operator()(int idx, int b) const {
+    C v; v.x = 0; v.y = 0;
+    if (TF_IN(kSiteSmem + 100, idx * ld + b, ext)) v = p[idx * ld + b];
+    return v;
+  }
 };
 template <typename C> struct SmemStore {
-  C* p; int ld;
-  __device__ __forceinline__ void operator()(int idx, int b, C v) const { p[idx * ld + b] = v; }
+  C* p; int ld; int ext;
+  __device__ __forceinline__ void operator()(int idx, int b, C v) const {
+    if (TF_IN(kSiteSmem + 100, idx * ld + b, ext)) p[idx * ld + b] = v;
+  }
 };
 
 // Full transform: pass 0 reads through `first`, the last pass writes through `last`,
@@ -215,8 +223,8 @@ __device__ __forceinline__ void fft_run(const FftPlan& P, const C* tw, C* bufA, 
     const int nb = P.n / R;
     const int Ns = P.ns[p];
     const C* twp = tw + P.tw_off[p];
-    SmemLoad<C> sl{(p & 1) ? bufA : bufB, ld};
-    SmemStore<C> ss{(p & 1) ? bufB : bufA, ld};
+    SmemLoad<C> sl{(p & 1) ? bufA : bufB, ld, P.n * ld};
+    SmemStore<C> ss{(p & 1) ? bufB : bufA, ld, P.n * ld};
     const bool f = (p == 0), l = (p == P.np - 1);
     if (f && l) fft_pass_any<INV>(R, nb, Ns, tbs, twp, first, last);
     else if (f) fft_pass_any<INV>(R, nb, Ns, tbs, twp, first, ss);

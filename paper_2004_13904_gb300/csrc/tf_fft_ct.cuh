@@ -1,0 +1,166 @@
+// Compile-time-sized Stockham FFT passes (device code) for the product kernels.
+//
+// Same transform as tf_fft.cuh (a batch of TB interleaved length-N sequences in a
+// [N][TB] shared-memory array, radix-R passes with Stockham's self-sorting index), but
+// N, the radix list, every stride and the thread count are template constants, so the
+// index arithmetic folds to shifts and constant multiplies.  Each thread transforms V
+// adjacent sequences at once: they share the twiddle factors and move through shared
+// memory as one 8*V-byte access.  Passes are in place: a thread loads its inputs,
+// computes, waits at a barrier, then stores, so one buffer serves all passes.
+#pragma once
+#include <type_traits>
+
+#include "tf_check.cuh"
+#include "tf_fft.cuh"
+
+namespace tfk {
+namespace ct {
+
+// V consecutive complex values to / from shared memory
+template <int V, typename C> struct Vec {
+  static __device__ __forceinline__ void ld(const C* p, C* o) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) o[i] = p[i];
+  }
+  static __device__ __forceinline__ void st(C* p, const C* v) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) p[i] = v[i];
+  }
+};
+template <> struct Vec<2, float2> {
+  static __device__ __forceinline__ void ld(const float2* p, float2* o) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = make_float2(t.x, t.y);
+    o[1] = make_float2(t.z, t.w);
+  }
+  static __device__ __forceinline__ void st(float2* p, const float2* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  }
+};
+template <> struct Vec<4, float2> {
+  static __device__ __forceinline__ void ld(const float2* p, float2* o) {
+    Vec<2, float2>::ld(p, o);
+    Vec<2, float2>::ld(p + 2, o + 2);
+  }
+  static __device__ __forceinline__ void st(float2* p, const float2* v) {
+    Vec<2, float2>::st(p, v);
+    Vec<2, float2>::st(p + 2, v + 2);
+  }
+};
+
+// Position of sequence b at element idx in the [N][TB] working buffer.  The sequence
+// index is XOR-swizzled by an even function of idx, so that walking idx at fixed b (the
+// staging and unpacking phases) spreads over the shared-memory banks instead of hitting
+// one bank group, while pairs (2k, 2k+1) stay adjacent for 16-byte accesses.
+template <typename C, int TB> __host__ __device__ constexpr int swz(int idx) {
+  constexpr int rows_per_line = (int)(128 / (TB * sizeof(C))) > 1 ? (int)(128 / (TB * sizeof(C))) : 1;
+  return TB >= 4 ? ((idx / rows_per_line) & (TB / 2 - 1)) << 1 : 0;
+}
+template <typename C, int TB> __device__ __forceinline__ int at(int idx, int b) {
+  return idx * TB + (b ^ swz<C, TB>(idx));
+}
+
+// The working buffer: [N][TB] complex, sequence index fastest (swizzled).
+template <typename C, int TB, int V> struct Buf {
+  static constexpr bool kIsBuf = true;
+  C* p;
+  int ext;  // elements of the buffer (checked builds test every access against it)
+  __device__ __forceinline__ void operator()(int idx, int b0, C* o) const {
+    const int e = at<C, TB>(idx, b0);
+    if (TF_IN(kSiteSmem, e + V - 1, ext) && TF_IN(kSiteSmem, e, ext)) Vec<V, C>::ld(p + e, o);
+  }
+  __device__ __forceinline__ void operator()(int idx, int b0, const C* v, int) const {
+    const int e = at<C, TB>(idx, b0);
+    if (TF_IN(kSiteSmem, e + V - 1, ext) && TF_IN(kSiteSmem, e, ext)) Vec<V, C>::st(p + e, v);
+  }
+};
+
+template <class T, class = void> struct IsBuf : std::false_type {};
+template <class T> struct IsBuf<T, std::void_t<decltype(T::kIsBuf)>> : std::true_type {};
+
+// One radix-R pass with stride Ns over TB sequences, V per thread, NT threads.
+// Loader: ld(idx, b0, C out[V]); storer: st(idx, b0, const C in[V], 0).
+template <int R, int Ns, int N, int TB, int V, int NT, bool INV, typename C, class L, class S>
+__device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, const S& st) {
+  constexpr int NB = N / R;
+  constexpr int G = TB / V;
+  constexpr int TOTAL = NB * G;
+  constexpr int ITER = (TOTAL + NT - 1) / NT;
+  constexpr bool kInPlace = IsBuf<L>::value && IsBuf<S>::value;
+  C v[ITER][V][R];
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int u = threadIdx.x + it * NT;
+    if (TOTAL % NT == 0 || u < TOTAL) {
+      const int j = u / G, b0 = (u % G) * V;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C t[V];
+        ld(j + r * NB, b0, t);
+#pragma unroll
+        for (int q = 0; q < V; ++q) v[it][q][r] = t[q];
+      }
+      if (Ns > 1) {
+        const int k = j % Ns;
+        const C* w = tw + k * (R - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C f = mk<C>(1, 0);
+          if (TF_IN(kSiteSmem + 1, (int)(w - tw) + r - 1, Ns * (R - 1))) f = w[r - 1];
+          if (INV) f.y = -f.y;
+#pragma unroll
+          for (int q = 0; q < V; ++q) v[it][q][r] = cmul(v[it][q][r], f);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < V; ++q) Dft<R, INV, C>::run(v[it][q]);
+    }
+  }
+  if (kInPlace) __syncthreads();
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int u = threadIdx.x + it * NT;
+    if (TOTAL % NT == 0 || u < TOTAL) {
+      const int j = u / G, b0 = (u % G) * V;
+      const int k = j % Ns;
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C t[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) t[q] = v[it][q][r];
+        st(base + r * Ns, b0, t, 0);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Passes of a radix list; pass 0 loads through `first`, the last pass stores through
+// `last`, the others use the shared buffer.  Twiddle layout as in FftPlan.
+template <int N, int Ns, int TwOff, int... Rs> struct Run;
+template <int N, int Ns, int TwOff, int R, int... Rest> struct Run<N, Ns, TwOff, R, Rest...> {
+  template <int TB, int V, int NT, bool INV, bool FIRST, typename C, class L0, class SL>
+  static __device__ __forceinline__ void go(const C* tw, C* buf, const L0& first, const SL& last) {
+    constexpr bool LAST = sizeof...(Rest) == 0;
+    const Buf<C, TB, V> b{buf, N * TB};
+    if constexpr (FIRST && LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, first, last);
+    else if constexpr (FIRST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, first, b);
+    else if constexpr (LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, last);
+    else pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, b);
+    if constexpr (!LAST)
+      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false>(
+          tw, buf, first, last);
+  }
+};
+
+template <int N, int... Rs> struct Plan {
+  static constexpr int n = N;
+  template <int TB, int V, int NT, bool INV, typename C, class L0, class SL>
+  static __device__ __forceinline__ void run(const C* tw, C* buf, const L0& first, const SL& last) {
+    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true>(tw, buf, first, last);
+  }
+};
+
+}  // namespace ct
+}  // namespace tfk

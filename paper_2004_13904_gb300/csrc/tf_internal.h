@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tf_check.cuh"
 #include "tf_fft.cuh"
 
 namespace tfk {
@@ -68,6 +69,30 @@ template <typename T> cudaError_t launch_rows_r2c(const RowsR2C<T>& a, int ncols
 template <typename T> cudaError_t launch_rows_c2r(const RowsC2R<T>& a, int ncols, int tb, cudaStream_t s);
 template <typename T> cudaError_t launch_cols_fwd(const ColsFwd<T>& a, int ncols, int tk, cudaStream_t s);
 template <typename T> cudaError_t launch_cols_adj(const ColsAdj<T>& a, int ncols, int tk, cudaStream_t s);
+// Compile-time-plan variants of the four product stages (tf_ct_kernels.cuh); they
+// return cudaErrorNotSupported, before any CUDA call, for lengths off their menu.
+template <typename T> cudaError_t ct_rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s);
+template <typename T> cudaError_t ct_rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s);
+template <typename T> cudaError_t ct_cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s);
+template <typename T> cudaError_t ct_cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s);
+template <> cudaError_t ct_rows_r2c<float>(const RowsR2C<float>&, int, cudaStream_t);
+template <> cudaError_t ct_rows_r2c<double>(const RowsR2C<double>&, int, cudaStream_t);
+template <> cudaError_t ct_rows_c2r<float>(const RowsC2R<float>&, int, cudaStream_t);
+template <> cudaError_t ct_rows_c2r<double>(const RowsC2R<double>&, int, cudaStream_t);
+template <> cudaError_t ct_cols_fwd<float>(const ColsFwd<float>&, int, cudaStream_t);
+template <> cudaError_t ct_cols_fwd<double>(const ColsFwd<double>&, int, cudaStream_t);
+template <> cudaError_t ct_cols_adj<float>(const ColsAdj<float>&, int, cudaStream_t);
+template <> cudaError_t ct_cols_adj<double>(const ColsAdj<double>&, int, cudaStream_t);
+// Transform lengths that have compile-time plans (ascending), with their radix lists.
+int ct_menu_count();
+int ct_menu_length(int i);
+int ct_menu_radices(int i, int* radices /* up to kMaxPass */);
+
+// Bounds-check records of each kernel translation unit (false in unchecked builds).
+bool oob_read_generic(OobRecord* out, bool clear);
+bool oob_read_ct_f32(OobRecord* out, bool clear);
+bool oob_read_ct_f64(OobRecord* out, bool clear);
+
 cudaError_t launch_table(const TableArgs& a, cudaStream_t s);
 cudaError_t launch_spectrum(const SpecArgs& a, int tk, cudaStream_t s);
 cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t count, cudaStream_t s);

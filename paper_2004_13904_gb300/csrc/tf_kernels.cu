@@ -11,6 +11,7 @@
 
 #include <algorithm>
 
+#include "tf_check.cuh"
 #include "tf_internal.h"
 
 namespace tfk {
@@ -44,25 +45,26 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(const RowsR2C<T> a) {
     const int pp = u / N, n = u - pp * N;
     const int ra = 2 * (pair0 + pp), rb = ra + 1;
     const int e = n - a.seq_off;
+    const int64_t ext = (int64_t)a.nrows * a.row_len;
     T xa = T(0), xb = T(0);
     if (e >= 0 && e < a.row_len) {
       if (ra < a.nrows) {
         const int64_t o = (int64_t)ra * a.row_len + e;
-        xa = src[o];
-        if (a.scale) xa *= a.scale[o];
+        if (TF_IN(100 + kSiteR2cSrc, o, ext)) xa = src[o];
+        if (a.scale && TF_IN(100 + kSiteR2cScale, o, ext)) xa *= a.scale[o];
       }
       if (rb < a.nrows) {
         const int64_t o = (int64_t)rb * a.row_len + e;
-        xb = src[o];
-        if (a.scale) xb *= a.scale[o];
+        if (TF_IN(100 + kSiteR2cSrc, o, ext)) xb = src[o];
+        if (a.scale && TF_IN(100 + kSiteR2cScale, o, ext)) xb *= a.scale[o];
       }
     }
     bufB[n * ld + pp] = mk<C>(xa, xb);
   }
   __syncthreads();
   C* fin = ((a.plan.np - 1) & 1) ? bufB : bufA;
-  fft_run<false>(a.plan, tw, bufA, bufB, ld, Log2<TB>::value, SmemLoad<C>{bufB, ld},
-                 SmemStore<C>{fin, ld});
+  fft_run<false>(a.plan, tw, bufA, bufB, ld, Log2<TB>::value, SmemLoad<C>{bufB, ld, N * ld},
+                 SmemStore<C>{fin, ld, N * ld});
   // split the packed transform into the two rows' half spectra
   C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int nh = a.nh;
@@ -73,8 +75,10 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(const RowsR2C<T> a) {
     const C z = fin[k * ld + pp];
     C zc = fin[(k ? N - k : 0) * ld + pp];
     zc.y = -zc.y;
-    dst[(int64_t)ra * nh + k] = mk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
-    if (rb < a.nrows)
+    const int64_t ext = (int64_t)a.nrows * nh;
+    if (TF_IN(100 + kSiteR2cDst, (int64_t)ra * nh + k, ext))
+      dst[(int64_t)ra * nh + k] = mk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
+    if (rb < a.nrows && TF_IN(100 + kSiteR2cDst, (int64_t)rb * nh + k, ext))
       dst[(int64_t)rb * nh + k] = mk<C>(T(0.5) * (z.y - zc.y), T(-0.5) * (z.x - zc.x));
   }
 }
@@ -97,8 +101,10 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r(const RowsC2R<T> a) {
   for (int u = threadIdx.x; u < TB * nh; u += blockDim.x) {
     const int pp = u / nh, k = u - pp * nh;
     const int ra = 2 * (pair0 + pp), rb = ra + 1;
-    C xa = ra < a.nrows ? src[(int64_t)ra * nh + k] : czero<C>();
-    C xb = rb < a.nrows ? src[(int64_t)rb * nh + k] : czero<C>();
+    const int64_t ext = (int64_t)a.nrows * nh;
+    C xa = czero<C>(), xb = czero<C>();
+    if (ra < a.nrows && TF_IN(100 + kSiteC2rSrc, (int64_t)ra * nh + k, ext)) xa = src[(int64_t)ra * nh + k];
+    if (rb < a.nrows && TF_IN(100 + kSiteC2rSrc, (int64_t)rb * nh + k, ext)) xb = src[(int64_t)rb * nh + k];
     const bool self = (k == 0) || (2 * k == N);
     if (self) { xa.y = T(0); xb.y = T(0); }
     bufB[k * ld + pp] = mk<C>(xa.x - xb.y, xa.y + xb.x);
@@ -106,8 +112,8 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r(const RowsC2R<T> a) {
   }
   __syncthreads();
   C* fin = ((a.plan.np - 1) & 1) ? bufB : bufA;
-  fft_run<true>(a.plan, tw, bufA, bufB, ld, Log2<TB>::value, SmemLoad<C>{bufB, ld},
-                SmemStore<C>{fin, ld});
+  fft_run<true>(a.plan, tw, bufA, bufB, ld, Log2<TB>::value, SmemLoad<C>{bufB, ld, N * ld},
+                SmemStore<C>{fin, ld, N * ld});
   T* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int L = a.out_len;
   for (int u = threadIdx.x; u < TB * L; u += blockDim.x) {
@@ -115,11 +121,14 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r(const RowsC2R<T> a) {
     const int ra = 2 * (pair0 + pp), rb = ra + 1;
     if (ra >= a.nrows) continue;
     const C z = fin[(a.seq_off + i) * ld + pp];
+    const int64_t ext = (int64_t)a.nrows * L;
     const int64_t oa = (int64_t)ra * L + i;
-    dst[oa] = a.scale ? z.x * a.scale[oa] : z.x;
+    if (TF_IN(100 + kSiteC2rDst, oa, ext))
+      dst[oa] = (a.scale && TF_IN(100 + kSiteC2rScale, oa, ext)) ? z.x * a.scale[oa] : z.x;
     if (rb < a.nrows) {
       const int64_t ob = (int64_t)rb * L + i;
-      dst[ob] = a.scale ? z.y * a.scale[ob] : z.y;
+      if (TF_IN(100 + kSiteC2rDst, ob, ext))
+        dst[ob] = (a.scale && TF_IN(100 + kSiteC2rScale, ob, ext)) ? z.y * a.scale[ob] : z.y;
     }
   }
 }
@@ -139,17 +148,23 @@ __global__ void __launch_bounds__(kThreads) k_cols_fwd(const ColsFwd<T> a) {
   const int k0 = blockIdx.x * TK;
   const int nh = a.nh, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
+  const int64_t z_ext = (int64_t)a.nz * ny * nh, g_ext = (int64_t)a.nz * N * nh;
+  const C* spec = a.spec;
   for (int r = 0; r < a.nz; ++r) {
-    const C* zr = z + (int64_t)r * ny * nh;
-    const C* gr = a.spec + (int64_t)r * N * nh;
+    const int64_t zoff = (int64_t)r * ny * nh, goff = (int64_t)r * N * nh;
     const bool first_layer = (r == 0);
     auto load = [=](int idx, int tk) -> C {
       const int k1 = k0 + tk;
-      return (idx < ny && k1 < nh) ? zr[(int64_t)idx * nh + k1] : czero<C>();
+      const int64_t e = zoff + (int64_t)idx * nh + k1;
+      C v = czero<C>();
+      if (idx < ny && k1 < nh && TF_IN(100 + kSiteFwdZ, e, z_ext)) v = z[e];
+      return v;
     };
     auto mac = [=](int idx, int tk, C v) {
       const int k1 = k0 + tk;
-      const C g = k1 < nh ? gr[(int64_t)idx * nh + k1] : czero<C>();
+      const int64_t e = goff + (int64_t)idx * nh + k1;
+      C g = czero<C>();
+      if (k1 < nh && TF_IN(100 + kSiteFwdSpec, e, g_ext)) g = spec[e];
       const C p = cmul(g, v);
       C* d = acc + idx * TK + tk;
       *d = first_layer ? p : cadd(*d, p);
@@ -157,11 +172,13 @@ __global__ void __launch_bounds__(kThreads) k_cols_fwd(const ColsFwd<T> a) {
     fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, mac);
   }
   C* s = a.s + (int64_t)blockIdx.y * a.s_ld;
+  const int64_t s_ext = (int64_t)sy * nh;
   auto store = [=](int idx, int tk, C v) {
     const int j = idx - (ny - 1), k1 = k0 + tk;
-    if (j >= 0 && j < sy && k1 < nh) s[(int64_t)j * nh + k1] = v;
+    if (j >= 0 && j < sy && k1 < nh && TF_IN(100 + kSiteFwdS, (int64_t)j * nh + k1, s_ext))
+      s[(int64_t)j * nh + k1] = v;
   };
-  fft_run<true>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, SmemLoad<C>{acc, TK}, store);
+  fft_run<true>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, SmemLoad<C>{acc, TK, N * TK}, store);
 }
 
 template <typename T, int TK>
@@ -179,22 +196,31 @@ __global__ void __launch_bounds__(kThreads) k_cols_adj(const ColsAdj<T> a) {
   const int k0 = blockIdx.x * TK;
   const int nh = a.nh, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
+  const int64_t z_ext = (int64_t)sy * nh, g_ext = (int64_t)a.nz * N * nh;
+  const int64_t u_ext = (int64_t)a.nz * ny * nh;
+  const C* spec = a.spec;
   auto load = [=](int idx, int tk) -> C {
     const int j = idx - (ny - 1), k1 = k0 + tk;
-    return (j >= 0 && j < sy && k1 < nh) ? z[(int64_t)j * nh + k1] : czero<C>();
+    C v = czero<C>();
+    if (j >= 0 && j < sy && k1 < nh && TF_IN(100 + kSiteAdjZ, (int64_t)j * nh + k1, z_ext))
+      v = z[(int64_t)j * nh + k1];
+    return v;
   };
-  fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, SmemStore<C>{acc, TK});
+  fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, SmemStore<C>{acc, TK, N * TK});
   C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
   for (int r = 0; r < a.nz; ++r) {
-    const C* gr = a.spec + (int64_t)r * N * nh;
-    C* ur = u + (int64_t)r * ny * nh;
+    const int64_t goff = (int64_t)r * N * nh, uoff = (int64_t)r * ny * nh;
     auto prod = [=](int idx, int tk) -> C {
       const int k1 = k0 + tk;
-      return k1 < nh ? cmulc(acc[idx * TK + tk], gr[(int64_t)idx * nh + k1]) : czero<C>();
+      const int64_t e = goff + (int64_t)idx * nh + k1;
+      C v = czero<C>();
+      if (k1 < nh && TF_IN(100 + kSiteAdjSpec, e, g_ext)) v = cmulc(acc[idx * TK + tk], spec[e]);
+      return v;
     };
     auto store = [=](int idx, int tk, C v) {
       const int k1 = k0 + tk;
-      if (idx < ny && k1 < nh) ur[(int64_t)idx * nh + k1] = v;
+      const int64_t e = uoff + (int64_t)idx * nh + k1;
+      if (idx < ny && k1 < nh && TF_IN(100 + kSiteAdjU, e, u_ext)) u[e] = v;
     };
     fft_run<true>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, prod, store);
   }
@@ -481,5 +507,7 @@ cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t count, cudaSt
   k_to_f32<<<blocks, 256, 0, s>>>(src, dst, count);
   return cudaGetLastError();
 }
+
+TF_DEFINE_OOB_READER(oob_read_generic)
 
 }  // namespace tfk

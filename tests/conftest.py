@@ -24,3 +24,21 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _bounds_record(request):
+    """With TF_LIB_VARIANT=checked (bounds-checked library), fail any GPU test whose
+    kernels recorded an out-of-bounds access."""
+    yield
+    import os
+    if os.environ.get("TF_LIB_VARIANT") != "checked" or "gpu" not in request.keywords:
+        return
+    import ctypes
+    import torch
+    from paper_2004_13904_gb300 import _lib
+    torch.cuda.synchronize()
+    c, s, o, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+    _lib.lib().tf_debug_oob(ctypes.byref(c), ctypes.byref(s), ctypes.byref(o), ctypes.byref(e))
+    assert c.value == 1, "TF_LIB_VARIANT=checked but the library is not a checked build"
+    assert s.value == 0, f"out-of-bounds access: site {s.value}, offset {o.value}, extent {e.value}"

@@ -76,13 +76,16 @@ def make_op(g, kind, inc, dec, dtn):
     return Operator(g, kind, inc, dec, dtype=_dt(dtn))
 
 
+@pytest.mark.parametrize("engine", [0, 1], ids=["compiled", "generic"])
 @pytest.mark.parametrize("dtn", ["f64", "f32"])
 @pytest.mark.parametrize("case", SMALL, ids=[c[0] for c in SMALL])
-def test_products_match_dense(case, dtn):
+def test_products_match_dense(case, dtn, engine):
     torch = _torch()
     name, g, kind, inc, dec = case
     R = ref(name, g, kind, inc, dec)
     op = make_op(g, kind, inc, dec, dtn)
+    op.set_engine(engine)
+    assert op.engine()[0] == engine
     assert (op.m, op.n) == (g.m, g.n)
     rng = np.random.default_rng(1)
     B = 5
@@ -124,6 +127,7 @@ def test_tiles_and_ragged_chunks(tiles):
     name, g, kind, inc, dec = SMALL[7]
     R = ref(name, g, kind, inc, dec)
     op = make_op(g, kind, inc, dec, "f64")
+    op.set_engine(1)                            # tiles apply to the generic engine
     op.set_tuning(tiles[0], tiles[1], 3)        # chunks of 3 columns: 7 = 3 + 3 + 1
     assert op.tuning() == (tiles[0], tiles[1], 3)
     rng = np.random.default_rng(7)
@@ -165,6 +169,14 @@ def test_adjoint_identity_and_determinism_c3():
     rhs = float(x @ gty)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
     assert torch.equal(op.matvec(x), gx)         # bitwise re-run equality
+
+
+def test_compiled_plans_used_on_menu_sizes():
+    op = make_op(synth.config_grid("c2"), "gravity", 90.0, 0.0, "f32")
+    assert (op.n1, op.n2) == (224, 224)
+    assert op.engine() == (0, True, True)
+    op.set_engine(1)
+    assert op.engine() == (1, False, False)
 
 
 @pytest.mark.parametrize("dtn", ["f32", "f64"])
