@@ -45,7 +45,7 @@ NCU_TRAFFIC = {}
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("tf_kernels.cu", "tf_fft.cuh"):
+    for f in ("tf_kernels.cu", "tf_fft.cuh", "tf_ct_kernels.cuh", "tf_fft_ct.cuh"):
         with open(os.path.join(ROOT, "paper_2004_13904_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -196,8 +196,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -209,6 +209,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2004_13904_gb300 import Operator, STAGES
+    from paper_2004_13904_gb300.parallel import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -256,10 +257,7 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = op.profile_read()
     op.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     products = 2 * BLOCK * args.steps * world
     value = products / (ms / 1e3)
 
@@ -279,10 +277,7 @@ def main():
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dev)
     esz = 4 if dt == torch.float32 else 8
     e2e = {"value": 2 * BLOCK * args.e2e_steps * world / e2e_s, "unit": "products/s",
            "h2d_bytes_per_step": (g.n + g.m) * BLOCK * esz,
@@ -318,6 +313,8 @@ def main():
     gpu_launches = int(sum(v[1] for v in prof.values()))
 
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
         return
     line = {
         "metric": "G/G^T column products per second", "value": value, "unit": "products/s",
