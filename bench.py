@@ -40,12 +40,16 @@ WORKLOAD = ("c2 gravity: 100x100 stations, 110x110x10 cells of 50 m (5% padding)
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the
 # hash of the kernel sources at capture time (null once the kernels change).
-NCU_TRAFFIC = {}
+# cols_fwd, c2, FP32: 274 MB (DRAM read + write) for one 256-column launch, scaled to the
+# benchmark's 1260-column launch by columns (traffic grows in proportion).
+NCU_TRAFFIC = {
+    ("cols_fwd", "c2", "f32"): {"hash": "6c30a6ba251ab68e", "bytes_per_launch": 274.3e6 * 1260 / 256},
+}
 
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("tf_kernels.cu", "tf_fft.cuh", "tf_ct_kernels.cuh", "tf_fft_ct.cuh"):
+    for f in ("tf_ct_kernels.cuh", "tf_fft_ct.cuh", "tf_fft.cuh", "tf_check.cuh"):
         with open(os.path.join(ROOT, "paper_2004_13904_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -202,13 +206,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--columns", type=int, default=BLOCK,
+                    help="columns per block (default: the 1260-column RSVD block); smaller "
+                         "blocks serve profiling captures")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
 
     import torch
     import torch.distributed as dist
-    from paper_2004_13904_gb300 import Operator, STAGES
+    from paper_2004_13904_gb300 import Operator, STAGES, peak_tflops
     from paper_2004_13904_gb300.parallel import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,10 +233,11 @@ def main():
     g = synth.config_grid(CONFIG)
     op = Operator(g, "gravity", dtype=dt)
     dev = torch.device("cuda", local)
-    X = torch.tensor(synth.gaussian_columns(g.n, BLOCK, seed=123 + rank), dtype=dt, device=dev)
-    Y = torch.tensor(synth.gaussian_columns(g.m, BLOCK, seed=321 + rank), dtype=dt, device=dev)
-    D = torch.empty((BLOCK, g.m), dtype=dt, device=dev)
-    XT = torch.empty((BLOCK, g.n), dtype=dt, device=dev)
+    cols_per_rank = args.columns
+    X = torch.tensor(synth.gaussian_columns(g.n, cols_per_rank, seed=123 + rank), dtype=dt, device=dev)
+    Y = torch.tensor(synth.gaussian_columns(g.m, cols_per_rank, seed=321 + rank), dtype=dt, device=dev)
+    D = torch.empty((cols_per_rank, g.m), dtype=dt, device=dev)
+    XT = torch.empty((cols_per_rank, g.n), dtype=dt, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -258,30 +266,32 @@ def main():
     prof = op.profile_read()
     op.profile(False)
     ms = max_over_ranks(ms, dev)
-    products = 2 * BLOCK * args.steps * world
+    products = 2 * cols_per_rank * args.steps * world
     value = products / (ms / 1e3)
 
     # end to end through the public API with pinned host buffers
-    Xh = X.cpu().pin_memory()
-    Yh = Y.cpu().pin_memory()
-    Dh = torch.empty((BLOCK, g.m), dtype=dt, pin_memory=True)
-    XTh = torch.empty((BLOCK, g.n), dtype=dt, pin_memory=True)
-    op.matmat_host(Xh, Dh)
-    op.rmatmat_host(Yh, XTh)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    esz = 4 if dt == torch.float32 else 8
+    e2e = None
+    if args.e2e_steps > 0:
+        Xh = X.cpu().pin_memory()
+        Yh = Y.cpu().pin_memory()
+        Dh = torch.empty((cols_per_rank, g.m), dtype=dt, pin_memory=True)
+        XTh = torch.empty((cols_per_rank, g.n), dtype=dt, pin_memory=True)
         op.matmat_host(Xh, Dh)
         op.rmatmat_host(Yh, XTh)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    barrier()
-    e2e_s = max_over_ranks(e2e_s, dev)
-    esz = 4 if dt == torch.float32 else 8
-    e2e = {"value": 2 * BLOCK * args.e2e_steps * world / e2e_s, "unit": "products/s",
-           "h2d_bytes_per_step": (g.n + g.m) * BLOCK * esz,
-           "d2h_bytes_per_step": (g.m + g.n) * BLOCK * esz}
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            op.matmat_host(Xh, Dh)
+            op.rmatmat_host(Yh, XTh)
+            torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        e2e_s = max_over_ranks(e2e_s, dev)
+        e2e = {"value": 2 * cols_per_rank * args.e2e_steps * world / e2e_s, "unit": "products/s",
+               "h2d_bytes_per_step": (g.n + g.m) * cols_per_rank * esz,
+               "d2h_bytes_per_step": (g.m + g.n) * cols_per_rank * esz}
 
     # roofline of the dominant kernel, timed live with events on the launching stream
     model = stage_model(g)
@@ -292,24 +302,23 @@ def main():
     avg_s = tms / 1e3 / max(launches, 1)
     pk, pk_kind = peaks()
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    if dt == torch.float32:
-        peak = fp32_peak_tflops(sm_max)
-        achieved = flops * per_launch_cols / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
-    else:
-        peak = pk["hbm_gbs"]
-        achieved = bytes_ * per_launch_cols / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"hbm_gbs ({pk_kind})"}
+    measured = peak_tflops(dt)
+    achieved = flops * per_launch_cols / avg_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": measured, "unit": "TFLOP/s",
+            "frac": achieved / measured,
+            "peak_source": f"measured: FMA-chain probe in {args.dtype} on this GPU"
+                           + (f"; derived FP32 peak 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                              f"= {fp32_peak_tflops(sm_max):.1f}" if dt == torch.float32 else ""),
+            "hbm": {"achieved_gbs": bytes_ * per_launch_cols / avg_s / 1e9,
+                    "peak_gbs": pk["hbm_gbs"], "peak_source": f"hbm_gbs ({pk_kind})"}}
     tr = NCU_TRAFFIC.get((top, CONFIG, args.dtype))
-    roof["traffic"] = tr["bytes_per_launch"] if tr and tr["hash"] == kernel_hash() else None
+    ok = tr and tr["hash"] == kernel_hash() and cols_per_rank == BLOCK
+    roof["traffic"] = tr["bytes_per_launch"] if ok else None
     roof["kernel"] = top
     roof["launch_ms"] = avg_s * 1e3
     roof["columns_per_launch"] = per_launch_cols
     stage_share = {s: prof[s][0] / max(sum(v[0] for v in prof.values()), 1e-30) for s in STAGES}
-    hbm_alg = (4 * g.n + 4 * g.m) * 2 * BLOCK * args.steps / (ms / 1e3) / 1e9
+    hbm_alg = (esz * g.n + esz * g.m) * 2 * cols_per_rank * args.steps / (ms / 1e3) / 1e9
     gpu_launches = int(sum(v[1] for v in prof.values()))
 
     if rank != 0:
@@ -321,7 +330,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "block_columns": BLOCK, "fft": [op.n1, op.n2],
+        "config": {"workload": WORKLOAD, "block_columns": cols_per_rank, "fft": [op.n1, op.n2],
                    "tuning": list(op.tuning()),
                    "l2": "inputs (X 610 MB, Y 50 MB in FP32) exceed L2; no flush"},
         "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,

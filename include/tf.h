@@ -179,6 +179,12 @@ tf_status tf_matvec_noalloc(const tf_op* op, const void* x, void* d, const void*
  * within the column's buffer and that buffer's length.  Synchronises the device. */
 tf_status tf_debug_oob(int* checked, int* site, int64_t* offset, int64_t* extent);
 
+/* Measured arithmetic peak of the current device for dtype: a launch of 8 CTAs per SM,
+ * 256 threads each running 8 independent fused multiply-add chains, timed with CUDA
+ * events; *tflops = 2 flop x FMAs / time.  The denominator of ALU-bound rooflines.
+ * Synchronises the stream.  Errors: TF_EINVAL, TF_ENOMEM, TF_ECUDA. */
+tf_status tf_peak_probe(tf_dtype dtype, double* tflops, tf_stream stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* tf_last_error(void);
 

@@ -12,7 +12,7 @@ import ctypes
 from . import _lib
 from ._lib import TFError, TF_F32, TF_F64  # noqa: F401
 
-__all__ = ["Operator", "TFError", "STAGES"]
+__all__ = ["Operator", "TFError", "STAGES", "peak_tflops"]
 
 STAGES = ("rows_r2c_model", "cols_fwd", "rows_c2r_data",
           "rows_r2c_data", "cols_adj", "rows_c2r_model")
@@ -21,6 +21,16 @@ STAGES = ("rows_r2c_model", "cols_fwd", "rows_c2r_data",
 def _torch():
     import torch
     return torch
+
+
+def peak_tflops(dtype) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current GPU for torch.float32/float64."""
+    torch = _torch()
+    v = ctypes.c_double()
+    dt = TF_F32 if dtype == torch.float32 else TF_F64
+    _lib.check(_lib.lib().tf_peak_probe(dt, ctypes.byref(v),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return v.value
 
 
 class Operator:

@@ -60,6 +60,7 @@ SIGNATURES = {
     "tf_set_engine": [vp, c_int],
     "tf_get_engine": [vp, P(c_int), P(c_int), P(c_int)],
     "tf_debug_oob": [P(c_int), P(c_int), P(i64), P(i64)],
+    "tf_peak_probe": [c_int, P(ctypes.c_double), vp],
 }
 
 

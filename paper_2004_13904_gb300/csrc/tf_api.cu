@@ -668,6 +668,26 @@ tf_status tf_debug_oob(int* checked, int* site, int64_t* offset, int64_t* extent
   return TF_OK;
 }
 
+tf_status tf_peak_probe(tf_dtype dtype, double* tflops, tf_stream stream) {
+  if (!tflops) return fail(TF_EINVAL, "tflops is NULL");
+  if (dtype != TF_F32 && dtype != TF_F64) return fail(TF_EINVAL, "unknown dtype %d", (int)dtype);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device query");
+  const int blocks = sms * 8;
+  const int iters = dtype == TF_F32 ? 65536 : 4096;
+  void* out = nullptr;
+  e = cudaMalloc(&out, (size_t)blocks * 256 * 8);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(probe)");
+  float ms = 0;
+  e = tfk::launch_fma_probe(dtype == TF_F32 ? 0 : 1, out, blocks, iters, &ms, (cudaStream_t)stream);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "FMA probe");
+  *tflops = 2.0 * 8.0 * iters * (double)blocks * 256 / (ms * 1e-3) / 1e12;
+  return TF_OK;
+}
+
 const char* tf_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"

@@ -94,6 +94,8 @@ bool oob_read_ct_f32(OobRecord* out, bool clear);
 bool oob_read_ct_f64(OobRecord* out, bool clear);
 
 cudaError_t launch_table(const TableArgs& a, cudaStream_t s);
+// FMA-chain probe: two timed launches of `blocks` x 256 threads, 8 chains x iters each.
+cudaError_t launch_fma_probe(int dtype, void* out, int blocks, int iters, float* ms, cudaStream_t s);
 cudaError_t launch_spectrum(const SpecArgs& a, int tk, cudaStream_t s);
 cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t count, cudaStream_t s);
 

@@ -508,6 +508,47 @@ cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t count, cudaSt
   return cudaGetLastError();
 }
 
+// ---- FMA throughput probe -------------------------------------------------------------
+
+// Eight independent fused multiply-add chains per thread; the result is stored so that
+// nothing is optimised away.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T b, T c) {
+  T a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = T(threadIdx.x + k) * T(1e-6);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+cudaError_t fma_probe(void* out, int blocks, int iters, float* ms, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma_probe<T><<<blocks, 256, 0, s>>>((T*)out, iters, T(0.999999), T(1e-7));
+  cudaEventRecord(e0, s);
+  k_fma_probe<T><<<blocks, 256, 0, s>>>((T*)out, iters, T(0.999999), T(1e-7));
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
+cudaError_t launch_fma_probe(int dtype, void* out, int blocks, int iters, float* ms, cudaStream_t s) {
+  return dtype == 0 ? fma_probe<float>(out, blocks, iters, ms, s)
+                    : fma_probe<double>(out, blocks, iters, ms, s);
+}
+
 TF_DEFINE_OOB_READER(oob_read_generic)
 
 }  // namespace tfk
