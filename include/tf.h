@@ -179,6 +179,18 @@ tf_status tf_matvec_noalloc(const tf_op* op, const void* x, void* d, const void*
  * within the column's buffer and that buffer's length.  Synchronises the device. */
 tf_status tf_debug_oob(int* checked, int* site, int64_t* offset, int64_t* extent);
 
+/* Gram-Schmidt helpers for the projected solvers (Alg. 1 re-orthogonalisation; the
+ * paper uses MGS, these give one classical pass, applied twice for CGS2, or one MGS
+ * step with k = 1).  A is a stack of k vectors of length len, vector j at A + j*lda
+ * (dtype elements), DEVICE memory.
+ * tf_rows_dot:  y[j] = A_j . x for j < k, accumulated in FP64; y is a DEVICE double[k].
+ * tf_rows_axpy: x -= sum_j c[j] A_j, the sum accumulated in FP64; c a DEVICE double[k].
+ * Deterministic (fixed reduction order), stream-ordered.  Errors: TF_EINVAL. */
+tf_status tf_rows_dot(tf_dtype dtype, const void* A, int64_t lda, int64_t k, int64_t len,
+                      const void* x, double* y, tf_stream stream);
+tf_status tf_rows_axpy(tf_dtype dtype, const void* A, int64_t lda, int64_t k, int64_t len,
+                       const double* c, void* x, tf_stream stream);
+
 /* Measured arithmetic peak of the current device for dtype: a launch of 8 CTAs per SM,
  * 256 threads each running 8 independent fused multiply-add chains, timed with CUDA
  * events; *tflops = 2 flop x FMAs / time.  The denominator of ALU-bound rooflines.

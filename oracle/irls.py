@@ -203,6 +203,7 @@ class IRLSParams:
     upper: float = 1.0
     kmax: int = 25
     chi2_stop: bool = True       # Eq. (12); False runs exactly kmax iterations
+    alphas: Optional[List[float]] = None   # if given, alpha^(k) = alphas[k-1] (no UPRE)
 
 
 @dataclasses.dataclass
@@ -231,11 +232,12 @@ def irls(apply_G: Callable, apply_GT: Callable, d_obs: np.ndarray, sigma: np.nda
         def gtt(y):
             return winv * apply_GT(wd * y)
 
+        given = p.alphas[k - 1] if p.alphas is not None else None
         if p.solver == "gkb":
             f = gkb(gt, gtt, rt, p.tp, n)
             U, s, _ = np.linalg.svd(f.B, full_matrices=False)
             alpha = alpha_initial(n, m, s[:p.t]) if k == 1 else None
-            z, alpha, _ = gkb_solution(f, p.t, alpha)
+            z, alpha, _ = gkb_solution(f, p.t, given if given is not None else alpha)
         else:
             f = rsvd(gt, gtt, omega)
             if k == 1:
@@ -243,7 +245,7 @@ def irls(apply_G: Callable, apply_GT: Callable, d_obs: np.ndarray, sigma: np.nda
                 alpha = alpha_initial(n, m, St)
             else:
                 alpha = None
-            z, alpha, _ = rsvd_solution(f, rt, p.t, alpha)
+            z, alpha, _ = rsvd_solution(f, rt, p.t, given if given is not None else alpha)
         m_new = np.clip(m_prev + winv * z, p.lower, p.upper)
         res = wd * (apply_G(m_new) - d_obs)
         chi2 = float(res @ res)

@@ -61,6 +61,8 @@ SIGNATURES = {
     "tf_get_engine": [vp, P(c_int), P(c_int), P(c_int)],
     "tf_debug_oob": [P(c_int), P(c_int), P(i64), P(i64)],
     "tf_peak_probe": [c_int, P(ctypes.c_double), vp],
+    "tf_rows_dot": [c_int, vp, i64, i64, i64, vp, vp, vp],
+    "tf_rows_axpy": [c_int, vp, i64, i64, i64, vp, vp, vp],
 }
 
 

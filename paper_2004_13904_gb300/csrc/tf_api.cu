@@ -668,6 +668,25 @@ tf_status tf_debug_oob(int* checked, int* site, int64_t* offset, int64_t* extent
   return TF_OK;
 }
 
+tf_status tf_rows_dot(tf_dtype dtype, const void* A, int64_t lda, int64_t k, int64_t len,
+                      const void* x, double* y, tf_stream stream) {
+  if (dtype != TF_F32 && dtype != TF_F64) return fail(TF_EINVAL, "unknown dtype %d", (int)dtype);
+  if (k < 0 || len < 0 || (k > 1 && lda < len)) return fail(TF_EINVAL, "need k, len >= 0 and lda >= len");
+  if (k > 0 && (!A || !x || !y)) return fail(TF_EINVAL, "A, x and y must be non-NULL");
+  if (k > 2147483647LL) return fail(TF_EINVAL, "k too large");
+  cudaError_t e = tfk::launch_rows_dot(dtype == TF_F32 ? 0 : 1, A, lda, k, len, x, y, (cudaStream_t)stream);
+  return e == cudaSuccess ? TF_OK : cuda_fail(e, "rows_dot launch");
+}
+
+tf_status tf_rows_axpy(tf_dtype dtype, const void* A, int64_t lda, int64_t k, int64_t len,
+                       const double* c, void* x, tf_stream stream) {
+  if (dtype != TF_F32 && dtype != TF_F64) return fail(TF_EINVAL, "unknown dtype %d", (int)dtype);
+  if (k < 0 || len < 0 || (k > 1 && lda < len)) return fail(TF_EINVAL, "need k, len >= 0 and lda >= len");
+  if (k > 0 && len > 0 && (!A || !c || !x)) return fail(TF_EINVAL, "A, c and x must be non-NULL");
+  cudaError_t e = tfk::launch_rows_axpy(dtype == TF_F32 ? 0 : 1, A, lda, k, len, c, x, (cudaStream_t)stream);
+  return e == cudaSuccess ? TF_OK : cuda_fail(e, "rows_axpy launch");
+}
+
 tf_status tf_peak_probe(tf_dtype dtype, double* tflops, tf_stream stream) {
   if (!tflops) return fail(TF_EINVAL, "tflops is NULL");
   if (dtype != TF_F32 && dtype != TF_F64) return fail(TF_EINVAL, "unknown dtype %d", (int)dtype);

@@ -94,6 +94,12 @@ bool oob_read_ct_f32(OobRecord* out, bool clear);
 bool oob_read_ct_f64(OobRecord* out, bool clear);
 
 cudaError_t launch_table(const TableArgs& a, cudaStream_t s);
+// Re-orthogonalisation helpers on a stack of k vectors A[j*lda + i] (dtype 0: float,
+// 1: double), FP64 accumulation.
+cudaError_t launch_rows_dot(int dtype, const void* A, int64_t lda, int64_t k, int64_t len,
+                            const void* x, double* y, cudaStream_t s);
+cudaError_t launch_rows_axpy(int dtype, const void* A, int64_t lda, int64_t k, int64_t len,
+                             const double* c, void* x, cudaStream_t s);
 // FMA-chain probe: two timed launches of `blocks` x 256 threads, 8 chains x iters each.
 cudaError_t launch_fma_probe(int dtype, void* out, int blocks, int iters, float* ms, cudaStream_t s);
 cudaError_t launch_spectrum(const SpecArgs& a, int tk, cudaStream_t s);

@@ -508,6 +508,58 @@ cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t count, cudaSt
   return cudaGetLastError();
 }
 
+// ---- re-orthogonalisation kernels ------------------------------------------------------
+
+// y[j] = sum_i A[j*lda + i] * x[i] for j < k, accumulated in FP64: one CTA per row,
+// fixed reduction order (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_dot(const T* __restrict__ A, int64_t lda, int64_t len,
+                                                  const T* __restrict__ x, double* __restrict__ y) {
+  const T* a = A + (int64_t)blockIdx.x * lda;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) acc += (double)a[i] * (double)x[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += part[w];
+    y[blockIdx.x] = sum;
+  }
+}
+
+// x[i] -= sum_j c[j] * A[j*lda + i] for j < k, the sum accumulated in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_axpy(const T* __restrict__ A, int64_t lda, int64_t k,
+                                                   int64_t len, const double* __restrict__ c,
+                                                   T* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t j = 0; j < k; ++j) acc += c[j] * (double)A[j * lda + i];
+    x[i] = (T)((double)x[i] - acc);
+  }
+}
+
+cudaError_t launch_rows_dot(int dtype, const void* A, int64_t lda, int64_t k, int64_t len,
+                            const void* x, double* y, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  if (dtype == 0) k_rows_dot<float><<<(unsigned)k, 256, 0, s>>>((const float*)A, lda, len, (const float*)x, y);
+  else k_rows_dot<double><<<(unsigned)k, 256, 0, s>>>((const double*)A, lda, len, (const double*)x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_axpy(int dtype, const void* A, int64_t lda, int64_t k, int64_t len,
+                             const double* c, void* x, cudaStream_t s) {
+  if (k <= 0 || len <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<int64_t>((len + 255) / 256, 152 * 16);
+  if (dtype == 0) k_rows_axpy<float><<<blocks, 256, 0, s>>>((const float*)A, lda, k, len, c, (float*)x);
+  else k_rows_axpy<double><<<blocks, 256, 0, s>>>((const double*)A, lda, k, len, c, (double*)x);
+  return cudaGetLastError();
+}
+
 // ---- FMA throughput probe -------------------------------------------------------------
 
 // Eight independent fused multiply-add chains per thread; the result is stored so that
