@@ -165,8 +165,20 @@ def gkb_factor(op, rt: torch.Tensor, winv: torch.Tensor, wd: torch.Tensor, tp: i
     return GKB(A, B, rnorm)
 
 
+# Projected problems larger than this are decomposed on the GPU (cuSOLVER, FP64) rather
+# than on the host.
+_HOST_MAX = 512
+
+
+def _svd64(B: np.ndarray, device):
+    if B.shape[1] <= _HOST_MAX:
+        return np.linalg.svd(B, full_matrices=False)
+    U, s, Vh = torch.linalg.svd(torch.tensor(B, device=device), full_matrices=False)
+    return U.cpu().numpy(), s.cpu().numpy(), Vh.cpu().numpy()
+
+
 def gkb_solve(f: GKB, t: int, n: int, alpha: Optional[float] = None):
-    U, s, Vh = np.linalg.svd(f.B, full_matrices=False)
+    U, s, Vh = _svd64(f.B, f.A.device)
     coef = f.rnorm * U[0]
     if alpha is None:
         alpha = choose_alpha(s[:t], coef[:t])
@@ -196,8 +208,13 @@ def rsvd_factor(op, omega: torch.Tensor, winv: torch.Tensor, wd: torch.Tensor) -
 
 def rsvd_solve(f: RSVD, rt: torch.Tensor, t: int, n: int, alpha: Optional[float] = None):
     Bt = f.Bt.double()
-    M = (Bt @ Bt.T).cpu().numpy()
-    D, V = np.linalg.eigh((M + M.T) / 2.0)
+    M = Bt @ Bt.T
+    if M.shape[0] <= _HOST_MAX:
+        M = M.cpu().numpy()
+        D, V = np.linalg.eigh((M + M.T) / 2.0)
+    else:
+        D, V = torch.linalg.eigh((M + M.T) / 2.0)
+        D, V = D.cpu().numpy(), V.cpu().numpy()
     S = np.sqrt(np.abs(D))
     idx = np.argsort(-S, kind="stable")[:t]
     St, Vt = S[idx], V[:, idx]
@@ -266,7 +283,7 @@ def invert(op, grid, d_obs: torch.Tensor, sigma: torch.Tensor, opts: IRLSOptions
             f = gkb_factor(op, rt, winv, wd, opts.tp, opts.reorth)
             a0 = fixed
             if k == 1 and a0 is None:
-                s_all = np.linalg.svd(f.B, compute_uv=False)
+                s_all = _svd64(f.B, dev)[1]
                 a0 = _alpha_start(n, m, s_all[:opts.t])
             z, alpha, _ = gkb_solve(f, opts.t, n, a0)
         else:
