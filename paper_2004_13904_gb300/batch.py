@@ -1,0 +1,118 @@
+"""Many independent inversion problems at once: block products of uneven operators as
+one CUDA graph, and a measured choice of engine and chunk size per operator.
+
+Each problem keeps its own operator (grid, kernel, spectra).  ``ProblemBatch.capture``
+records every problem's G X and G^T Y into one CUDA graph, spreading the problems over
+a few streams that fork from and join the capturing stream, so that problems too small
+to fill the GPU run side by side and the whole batch costs one graph launch.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import torch
+
+__all__ = ["ProblemBatch", "tune", "TUNE_CACHE"]
+
+
+class ProblemBatch:
+    """Block products G_i X_i and G_i^T Y_i for operators ops[i], `columns` columns each."""
+
+    def __init__(self, ops: Sequence, columns: int, streams: int = 8, seed: int = 0):
+        self.ops = list(ops)
+        self.columns = columns
+        dev = self.ops[0].device
+        gen = torch.Generator(device=dev).manual_seed(seed)
+        self.X = [torch.randn(columns, op.n, generator=gen, device=dev, dtype=op.dtype)
+                  for op in self.ops]
+        self.Y = [torch.randn(columns, op.m, generator=gen, device=dev, dtype=op.dtype)
+                  for op in self.ops]
+        self.D = [torch.empty(columns, op.m, device=dev, dtype=op.dtype) for op in self.ops]
+        self.XT = [torch.empty(columns, op.n, device=dev, dtype=op.dtype) for op in self.ops]
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, streams))]
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+
+    @property
+    def products(self) -> int:
+        """Column products (G and G^T columns) per run of the batch."""
+        return 2 * self.columns * len(self.ops)
+
+    def _issue(self, forked: bool) -> None:
+        main = torch.cuda.current_stream()
+        if not forked:
+            for i, op in enumerate(self.ops):
+                op.matmat(self.X[i], out=self.D[i])
+                op.rmatmat(self.Y[i], out=self.XT[i])
+            return
+        for s in self.streams:
+            s.wait_stream(main)
+        for i, op in enumerate(self.ops):
+            with torch.cuda.stream(self.streams[i % len(self.streams)]):
+                op.matmat(self.X[i], out=self.D[i])
+                op.rmatmat(self.Y[i], out=self.XT[i])
+        for s in self.streams:
+            main.wait_stream(s)
+
+    def run_eager(self, forked: bool = False) -> None:
+        """One pass of all products launched directly (on one stream, or forked)."""
+        self._issue(forked)
+
+    def capture(self) -> None:
+        """Record the forked batch into a CUDA graph (after an eager pass that sizes every
+        operator's workspace, since no allocation may happen under capture)."""
+        self._issue(True)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._issue(True)
+        self.graph = g
+
+    def replay(self) -> None:
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+
+
+# (n1, n2, nz, dtype, columns) -> (engine, chunk)
+TUNE_CACHE: Dict[Tuple, Tuple[int, int]] = {}
+
+
+def _time(fn, reps: int = 3) -> float:
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune(op, columns: int, chunks: Optional[List[int]] = None) -> Tuple[int, int]:
+    """Measure G X + G^T Y on `columns` random columns for each engine (compile-time
+    plans / generic) and chunk size, apply and cache the fastest choice."""
+    key = (op.n1, op.n2, op.nz, str(op.dtype), columns)
+    if key in TUNE_CACHE:
+        engine, chunk = TUNE_CACHE[key]
+        op.set_engine(engine)
+        op.set_tuning(0, 0, chunk)
+        return engine, chunk
+    X = torch.randn(columns, op.n, device=op.device, dtype=op.dtype)
+    Y = torch.randn(columns, op.m, device=op.device, dtype=op.dtype)
+    chunks = chunks or sorted({max(1, columns // 4), max(1, columns // 2), columns})
+    best = None
+    for engine in (0, 1):
+        op.set_engine(engine)
+        for chunk in chunks:
+            op.set_tuning(0, 0, chunk)
+            ms = _time(lambda: (op.matmat(X), op.rmatmat(Y)))
+            if best is None or ms < best[0]:
+                best = (ms, engine, chunk)
+    _, engine, chunk = best
+    op.set_engine(engine)
+    op.set_tuning(0, 0, chunk)
+    TUNE_CACHE[key] = (engine, chunk)
+    return engine, chunk

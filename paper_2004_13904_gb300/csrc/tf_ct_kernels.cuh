@@ -3,6 +3,8 @@
 // tf_kernels.cu compute (same stages, same data layout, same twiddle tables); only the
 // index arithmetic is resolved at compile time.  Included by tf_ct_f32.cu / tf_ct_f64.cu.
 #pragma once
+#include <atomic>
+
 #include "tf_check.cuh"
 #include "tf_fft_ct.cuh"
 #include "tf_internal.h"
@@ -243,9 +245,17 @@ __global__ void __launch_bounds__(NT) k_cols_adj(const ColsAdj<T> a) {
   }
 }
 
-// Dynamic shared memory above 48 KB needs an opt-in.
-template <class K> inline cudaError_t set_smem(K kernel, size_t smem) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// Dynamic shared memory above 48 KB needs an opt-in; it is raised only when a launch needs
+// more than any earlier launch of the same kernel, so steady-state launches (and launches
+// under CUDA-graph capture) make no attribute call.
+template <auto Kernel> inline cudaError_t set_smem(size_t smem) {
+  static std::atomic<size_t> granted{0};   // one per kernel
+  size_t have = granted.load(std::memory_order_relaxed);
+  if (smem <= have) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    while (have < smem && !granted.compare_exchange_weak(have, smem)) {}
+  return e;
 }
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
@@ -265,9 +275,9 @@ template <int N> struct Tiles<double, N> {
 template <typename T, class P>
 cudaError_t rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
-  auto k = k_rows_r2c<T, P, TL::TB, TL::V, TL::NT>;
+  constexpr auto k = k_rows_r2c<T, P, TL::TB, TL::V, TL::NT>;
   const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB) * sizeof(typename CT<T>::C);
-  cudaError_t e = set_smem(k, sm);
+  cudaError_t e = set_smem<k>(sm);
   if (e != cudaSuccess) return e;
   k<<<dim3(cdiv((a.nrows + 1) / 2, TL::TB), ncols), TL::NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -275,9 +285,9 @@ cudaError_t rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
 template <typename T, class P>
 cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
-  auto k = k_rows_c2r<T, P, TL::TB, TL::V, TL::NT>;
+  constexpr auto k = k_rows_c2r<T, P, TL::TB, TL::V, TL::NT>;
   const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB) * sizeof(typename CT<T>::C);
-  cudaError_t e = set_smem(k, sm);
+  cudaError_t e = set_smem<k>(sm);
   if (e != cudaSuccess) return e;
   k<<<dim3(cdiv((a.nrows + 1) / 2, TL::TB), ncols), TL::NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -285,9 +295,9 @@ cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
 template <typename T, class P>
 cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
-  auto k = k_cols_fwd<T, P, TL::TB, TL::V, TL::NT>;
+  constexpr auto k = k_cols_fwd<T, P, TL::TB, TL::V, TL::NT>;
   const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
-  cudaError_t e = set_smem(k, sm);
+  cudaError_t e = set_smem<k>(sm);
   if (e != cudaSuccess) return e;
   k<<<dim3(cdiv(a.nh, TL::TB), ncols), TL::NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -295,9 +305,9 @@ cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
 template <typename T, class P>
 cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
-  auto k = k_cols_adj<T, P, TL::TB, TL::V, TL::NT>;
+  constexpr auto k = k_cols_adj<T, P, TL::TB, TL::V, TL::NT>;
   const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
-  cudaError_t e = set_smem(k, sm);
+  cudaError_t e = set_smem<k>(sm);
   if (e != cudaSuccess) return e;
   k<<<dim3(cdiv(a.nh, TL::TB), ncols), TL::NT, sm, s>>>(a);
   return cudaGetLastError();

@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "tf_check.cuh"
 #include "tf_internal.h"
@@ -385,9 +386,18 @@ __global__ void k_to_f32(const double2* __restrict__ src, float2* __restrict__ d
     dst[i] = make_float2((float)src[i].x, (float)src[i].y);
 }
 
-template <class K>
-cudaError_t prep(K kernel, size_t smem) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// Raises a kernel's dynamic shared-memory limit when a launch needs more than any
+// earlier one did, so that steady-state launches (and launches under CUDA-graph
+// capture) make no attribute call.
+template <auto Kernel>
+cudaError_t prep(size_t smem) {
+  static std::atomic<size_t> granted{0};   // one per kernel
+  size_t have = granted.load(std::memory_order_relaxed);
+  if (smem <= have) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    while (have < smem && !granted.compare_exchange_weak(have, smem)) {}
+  return e;
 }
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
@@ -404,7 +414,7 @@ size_t smem_cols(int n, int tw_count, int tk, size_t csize) {
 template <typename T, int TB>
 static cudaError_t rows_r2c_tb(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
   const size_t sm = smem_rows(a.plan.n, a.plan.tw_count, TB, sizeof(typename CT<T>::C));
-  cudaError_t e = prep(k_rows_r2c<T, TB>, sm);
+  cudaError_t e = prep<k_rows_r2c<T, TB>>(sm);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div((a.nrows + 1) / 2, TB), ncols);
   k_rows_r2c<T, TB><<<grid, kThreads, sm, s>>>(a);
@@ -413,7 +423,7 @@ static cudaError_t rows_r2c_tb(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
 template <typename T, int TB>
 static cudaError_t rows_c2r_tb(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
   const size_t sm = smem_rows(a.plan.n, a.plan.tw_count, TB, sizeof(typename CT<T>::C));
-  cudaError_t e = prep(k_rows_c2r<T, TB>, sm);
+  cudaError_t e = prep<k_rows_c2r<T, TB>>(sm);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div((a.nrows + 1) / 2, TB), ncols);
   k_rows_c2r<T, TB><<<grid, kThreads, sm, s>>>(a);
@@ -422,7 +432,7 @@ static cudaError_t rows_c2r_tb(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
 template <typename T, int TK>
 static cudaError_t cols_fwd_tk(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
   const size_t sm = smem_cols(a.plan.n, a.plan.tw_count, TK, sizeof(typename CT<T>::C));
-  cudaError_t e = prep(k_cols_fwd<T, TK>, sm);
+  cudaError_t e = prep<k_cols_fwd<T, TK>>(sm);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(a.nh, TK), ncols);
   k_cols_fwd<T, TK><<<grid, kThreads, sm, s>>>(a);
@@ -431,7 +441,7 @@ static cudaError_t cols_fwd_tk(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
 template <typename T, int TK>
 static cudaError_t cols_adj_tk(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
   const size_t sm = smem_cols(a.plan.n, a.plan.tw_count, TK, sizeof(typename CT<T>::C));
-  cudaError_t e = prep(k_cols_adj<T, TK>, sm);
+  cudaError_t e = prep<k_cols_adj<T, TK>>(sm);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(a.nh, TK), ncols);
   k_cols_adj<T, TK><<<grid, kThreads, sm, s>>>(a);
@@ -495,7 +505,7 @@ cudaError_t launch_spectrum(const SpecArgs& a, int tk, cudaStream_t s) {
   (void)tk;
   constexpr int TK = 4;
   const size_t sm = ((size_t)tw_pad(a.plan.tw_count) + 2 * (size_t)a.plan.n * TK) * sizeof(double2);
-  cudaError_t e = prep(k_spectrum<TK>, sm);
+  cudaError_t e = prep<k_spectrum<TK>>(sm);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(a.nh, TK), a.nz);
   k_spectrum<TK><<<grid, kThreads, sm, s>>>(a);
