@@ -183,8 +183,11 @@ tf_status tf_debug_oob(int* checked, int* site, int64_t* offset, int64_t* extent
  * paper uses MGS, these give one classical pass, applied twice for CGS2, or one MGS
  * step with k = 1).  A is a stack of k vectors of length len, vector j at A + j*lda
  * (dtype elements), DEVICE memory.
- * tf_rows_dot:  y[j] = A_j . x for j < k, accumulated in FP64; y is a DEVICE double[k].
- * tf_rows_axpy: x -= sum_j c[j] A_j, the sum accumulated in FP64; c a DEVICE double[k].
+ * tf_rows_dot:  y[j] = A_j . x for j < k; y is a DEVICE double[k].
+ * tf_rows_axpy: x -= sum_j c[j] A_j; c is a DEVICE double[k].
+ * Sums are accumulated in FP64 for TF_F64 data and in double-float arithmetic (pairs of
+ * floats combined with exact TwoSum/TwoProd steps, about 44 significant bits) for TF_F32
+ * data, which keeps them on the FP32 pipe.
  * Deterministic (fixed reduction order), stream-ordered.  Errors: TF_EINVAL. */
 tf_status tf_rows_dot(tf_dtype dtype, const void* A, int64_t lda, int64_t k, int64_t len,
                       const void* x, double* y, tf_stream stream);

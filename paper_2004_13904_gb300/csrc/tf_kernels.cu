@@ -520,14 +520,42 @@ cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t count, cudaSt
 
 // ---- re-orthogonalisation kernels ------------------------------------------------------
 
-// y[j] = sum_i A[j*lda + i] * x[i] for j < k, accumulated in FP64: one CTA per row,
-// fixed reduction order (deterministic).
-template <typename T>
-__global__ void __launch_bounds__(256) k_rows_dot(const T* __restrict__ A, int64_t lda, int64_t len,
-                                                  const T* __restrict__ x, double* __restrict__ y) {
-  const T* a = A + (int64_t)blockIdx.x * lda;
+// Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2 (about 44 bits).
+// Knuth's TwoSum and the FMA-based TwoProd give exact error terms on the FP32 pipe,
+// which on this GPU is far faster than its FP64 pipe.  The _rn intrinsics round each
+// step on its own (the compiler never fuses them into FMAs), which the error terms need.
+struct DF { float hi, lo; };
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {   // needs |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = df_two_sum(a.hi, b.hi);
+  const float t = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return df_fast_two_sum(s.hi, t);
+}
+__device__ __forceinline__ DF df_mul_ff(float a, float b) {   // exact product of floats
+  const float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ DF df_mul_df(DF c, float a) {      // (c.hi + c.lo) * a
+  const DF p = df_mul_ff(c.hi, a);
+  return df_fast_two_sum(p.hi, fmaf(c.lo, a, p.lo));
+}
+
+// y[j] = sum_i A[j*lda + i] * x[i] for j < k: one CTA per row, fixed reduction order
+// (deterministic).  Accumulation in FP64 for double data, in double-float for float data.
+__global__ void __launch_bounds__(256) k_rows_dot_d(const double* __restrict__ A, int64_t lda,
+                                                    int64_t len, const double* __restrict__ x,
+                                                    double* __restrict__ y) {
+  const double* a = A + (int64_t)blockIdx.x * lda;
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) acc += (double)a[i] * (double)x[i];
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) acc = fma(a[i], x[i], acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   __shared__ double part[8];
@@ -540,33 +568,99 @@ __global__ void __launch_bounds__(256) k_rows_dot(const T* __restrict__ A, int64
   }
 }
 
-// x[i] -= sum_j c[j] * A[j*lda + i] for j < k, the sum accumulated in FP64.
-template <typename T>
-__global__ void __launch_bounds__(256) k_rows_axpy(const T* __restrict__ A, int64_t lda, int64_t k,
-                                                   int64_t len, const double* __restrict__ c,
-                                                   T* __restrict__ x) {
+__global__ void __launch_bounds__(256) k_rows_dot_f(const float* __restrict__ A, int64_t lda,
+                                                    int64_t len, const float* __restrict__ x,
+                                                    double* __restrict__ y) {
+  const float* a = A + (int64_t)blockIdx.x * lda;
+  DF acc = {0.f, 0.f};
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) acc = df_add(acc, df_mul_ff(a[i], x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF other = {__shfl_down_sync(0xffffffffu, acc.hi, o), __shfl_down_sync(0xffffffffu, acc.lo, o)};
+    acc = df_add(acc, other);
+  }
+  __shared__ DF part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += (double)part[w].hi + (double)part[w].lo;
+    y[blockIdx.x] = sum;
+  }
+}
+
+// x[i] -= sum_j c[j] * A[j*lda + i] for j < k: FP64 accumulation for double data; for
+// float data the coefficients are split into float pairs in shared memory and the sum is
+// accumulated in double-float.
+__global__ void __launch_bounds__(256) k_rows_axpy_d(const double* __restrict__ A, int64_t lda,
+                                                     int64_t k, int64_t len,
+                                                     const double* __restrict__ c,
+                                                     double* __restrict__ x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int64_t j = 0; j < k; ++j) acc += c[j] * (double)A[j * lda + i];
-    x[i] = (T)((double)x[i] - acc);
+    for (int64_t j = 0; j < k; ++j) acc = fma(c[j], A[j * lda + i], acc);
+    x[i] -= acc;
+  }
+}
+
+constexpr int kAxpyTile = 2048;
+
+__global__ void __launch_bounds__(256) k_rows_axpy_f(const float* __restrict__ A, int64_t lda,
+                                                     int64_t k, int64_t len,
+                                                     const double* __restrict__ c,
+                                                     float* __restrict__ x) {
+  __shared__ DF cs[kAxpyTile];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  DF acc = {0.f, 0.f};
+  for (int64_t j0 = 0; j0 < k; j0 += kAxpyTile) {
+    const int nt = (int)((k - j0) < kAxpyTile ? (k - j0) : kAxpyTile);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+      const double v = c[j0 + t];
+      const float hi = (float)v;
+      cs[t] = {hi, (float)(v - (double)hi)};
+    }
+    __syncthreads();
+    if (i < len) {
+      const float* a = A + j0 * lda + i;
+      int t = 0;
+      for (; t + 4 <= nt; t += 4) {          // four independent loads in flight
+        const float a0 = a[(int64_t)t * lda], a1 = a[(int64_t)(t + 1) * lda];
+        const float a2 = a[(int64_t)(t + 2) * lda], a3 = a[(int64_t)(t + 3) * lda];
+        acc = df_add(acc, df_mul_df(cs[t], a0));
+        acc = df_add(acc, df_mul_df(cs[t + 1], a1));
+        acc = df_add(acc, df_mul_df(cs[t + 2], a2));
+        acc = df_add(acc, df_mul_df(cs[t + 3], a3));
+      }
+      for (; t < nt; ++t) acc = df_add(acc, df_mul_df(cs[t], a[(int64_t)t * lda]));
+    }
+  }
+  if (i < len) {
+    const DF r = df_add({x[i], 0.f}, {-acc.hi, -acc.lo});
+    x[i] = r.hi + r.lo;
   }
 }
 
 cudaError_t launch_rows_dot(int dtype, const void* A, int64_t lda, int64_t k, int64_t len,
                             const void* x, double* y, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  if (dtype == 0) k_rows_dot<float><<<(unsigned)k, 256, 0, s>>>((const float*)A, lda, len, (const float*)x, y);
-  else k_rows_dot<double><<<(unsigned)k, 256, 0, s>>>((const double*)A, lda, len, (const double*)x, y);
+  if (dtype == 0) k_rows_dot_f<<<(unsigned)k, 256, 0, s>>>((const float*)A, lda, len, (const float*)x, y);
+  else k_rows_dot_d<<<(unsigned)k, 256, 0, s>>>((const double*)A, lda, len, (const double*)x, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rows_axpy(int dtype, const void* A, int64_t lda, int64_t k, int64_t len,
                              const double* c, void* x, cudaStream_t s) {
   if (k <= 0 || len <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)std::min<int64_t>((len + 255) / 256, 152 * 16);
-  if (dtype == 0) k_rows_axpy<float><<<blocks, 256, 0, s>>>((const float*)A, lda, k, len, c, (float*)x);
-  else k_rows_axpy<double><<<blocks, 256, 0, s>>>((const double*)A, lda, k, len, c, (double*)x);
+  if (dtype == 0) {
+    // one element per thread so that every thread of a CTA meets the tile barriers
+    const unsigned blocks = (unsigned)((len + 255) / 256);
+    k_rows_axpy_f<<<blocks, 256, 0, s>>>((const float*)A, lda, k, len, c, (float*)x);
+  } else {
+    const unsigned blocks = (unsigned)std::min<int64_t>((len + 255) / 256, 152 * 16);
+    k_rows_axpy_d<<<blocks, 256, 0, s>>>((const double*)A, lda, k, len, c, (double*)x);
+  }
   return cudaGetLastError();
 }
 

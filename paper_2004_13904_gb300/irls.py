@@ -139,47 +139,95 @@ class GKB:
 
 def gkb_factor(op, rt: torch.Tensor, winv: torch.Tensor, wd: torch.Tensor, tp: int,
                reorth: str = "cgs2") -> GKB:
-    """Alg. 1: G~ A = H B, G~ = diag(wd) G diag(winv), with re-orthogonalisation."""
-    n, m = op.n, op.m
-    A = torch.zeros((tp, n), dtype=op.dtype, device=op.device)
-    H = torch.zeros((tp + 1, m), dtype=op.dtype, device=op.device)
-    B = np.zeros((tp + 1, tp))
-    beta = _norm64(rt)
-    H[0] = rt / beta
-    rnorm = beta
-    a = torch.zeros(n, dtype=op.dtype, device=op.device)
+    """Alg. 1: G~ A = H B, G~ = diag(wd) G diag(winv), with re-orthogonalisation.  The
+    norms stay on the device, so the loop does not wait for the host."""
+    n, m, dt, dev = op.n, op.m, op.dtype, op.device
+    A = torch.zeros((tp, n), dtype=dt, device=dev)
+    H = torch.zeros((tp + 1, m), dtype=dt, device=dev)
+    diag = torch.zeros(tp, dtype=torch.float64, device=dev)      # B(i, i) = gamma_i
+    sub = torch.zeros(tp, dtype=torch.float64, device=dev)       # B(i+1, i) = beta_{i+1}
+    beta = torch.linalg.vector_norm(rt, dtype=torch.float64)
+    rnorm = float(beta)
+    H[0] = rt / beta.to(dt)
+    a = torch.zeros(n, dtype=dt, device=dev)
     for i in range(tp):
         b = op.rmatvec(H[i], colscale=winv, rowscale=wd)
-        b -= beta * a
+        b -= beta.to(dt) * a
         _orthogonalise(A, i, b, reorth)
-        gamma = _norm64(b)
-        a = b / gamma
+        gamma = torch.linalg.vector_norm(b, dtype=torch.float64)
+        a = b / gamma.to(dt)
         A[i] = a
-        B[i, i] = gamma
+        diag[i] = gamma
         c = op.matvec(a, colscale=winv, rowscale=wd)
-        c -= gamma * H[i]
+        c -= gamma.to(dt) * H[i]
         _orthogonalise(H, i + 1, c, reorth)
-        beta = _norm64(c)
-        H[i + 1] = c / beta
-        B[i + 1, i] = beta
+        beta = torch.linalg.vector_norm(c, dtype=torch.float64)
+        H[i + 1] = c / beta.to(dt)
+        sub[i] = beta
+    B = np.zeros((tp + 1, tp))
+    idx = np.arange(tp)
+    B[idx, idx] = diag.cpu().numpy()
+    B[idx + 1, idx] = sub.cpu().numpy()
     return GKB(A, B, rnorm)
 
 
-# Projected problems larger than this are decomposed on the GPU (cuSOLVER, FP64) rather
-# than on the host.
+# Projected problems up to this size use a dense LAPACK SVD on the host; larger GKB
+# bidiagonals use the tridiagonal route below, larger RSVD Gram matrices cuSOLVER.
 _HOST_MAX = 512
 
 
-def _svd64(B: np.ndarray, device):
-    if B.shape[1] <= _HOST_MAX:
-        return np.linalg.svd(B, full_matrices=False)
-    U, s, Vh = torch.linalg.svd(torch.tensor(B, device=device), full_matrices=False)
-    return U.cpu().numpy(), s.cpu().numpy(), Vh.cpu().numpy()
+def _lower_to_upper(gam: np.ndarray, bet: np.ndarray):
+    """Givens rotations Q^T B = [R; 0] turning the lower bidiagonal (t_p+1) x t_p matrix
+    (diagonal gam, subdiagonal bet) into an upper bidiagonal R (diagonal d, superdiagonal
+    e); also returns q = Q^T e_1, whose first t_p entries are the first row of Q's leading
+    columns."""
+    n = gam.size
+    d = np.empty(n)
+    e = np.empty(max(n - 1, 0))
+    q = np.zeros(n + 1)
+    q[0] = 1.0
+    a = gam[0]
+    for i in range(n):
+        r = math.hypot(a, bet[i])
+        c, s_ = a / r, bet[i] / r
+        d[i] = r
+        if i + 1 < n:
+            e[i] = s_ * gam[i + 1]
+            a = c * gam[i + 1]
+        qi, qj = q[i], q[i + 1]
+        q[i], q[i + 1] = c * qi + s_ * qj, c * qj - s_ * qi
+    return d, e, q
 
 
-def gkb_solve(f: GKB, t: int, n: int, alpha: Optional[float] = None):
-    U, s, Vh = _svd64(f.B, f.A.device)
-    coef = f.rnorm * U[0]
+def bidiag_svd(B: np.ndarray):
+    """SVD pieces of the GKB bidiagonal B needed by the solve: (first row of U, singular
+    values descending, V^T).  Small B: dense LAPACK.  Large B: Givens reduction to an
+    upper bidiagonal R, then the eigen-decomposition of the 2n x 2n Golub-Kahan
+    tridiagonal matrix (zero diagonal, off-diagonals d1, e1, d2, ...; LAPACK dstevd),
+    whose eigenvectors for +sigma interleave (v_1, u_1, v_2, u_2, ...)/sqrt(2)."""
+    tp = B.shape[1]
+    if tp <= _HOST_MAX:
+        U, s, Vh = np.linalg.svd(B, full_matrices=False)
+        return U[0], s, Vh
+    from scipy.linalg import lapack
+    gam = np.diagonal(B).copy()
+    bet = np.diagonal(B, -1).copy()
+    d, e, q = _lower_to_upper(gam, bet)
+    off = np.empty(2 * tp - 1)
+    off[0::2] = d
+    off[1::2] = e
+    w, Z, info = lapack.dstevd(np.zeros(2 * tp), off, compute_v=1)
+    if info != 0:
+        raise RuntimeError(f"dstevd failed ({info})")
+    top = np.argsort(-w, kind="stable")[:tp]
+    Z = Z[:, top] * math.sqrt(2.0)
+    V, Ur = Z[0::2, :], Z[1::2, :]
+    return q[:tp] @ Ur, w[top], V.T
+
+
+def gkb_solve(f: GKB, t: int, n: int, alpha: Optional[float] = None, svd=None):
+    u1, s, Vh = svd if svd is not None else bidiag_svd(f.B)
+    coef = f.rnorm * u1
     if alpha is None:
         alpha = choose_alpha(s[:t], coef[:t])
     w = Vh.T @ (coef * s / (s * s + alpha * alpha))
@@ -250,6 +298,7 @@ class IRLSResult:
     alphas: List[float]
     chi2: List[float]
     seconds: List[float]
+    factor_seconds: List[float] = dataclasses.field(default_factory=list)
 
 
 def depth_weight_vector(grid, beta: float, dtype, device) -> torch.Tensor:
@@ -269,7 +318,7 @@ def invert(op, grid, d_obs: torch.Tensor, sigma: torch.Tensor, opts: IRLSOptions
     wz = depth_weight_vector(grid, opts.beta, dt, dev)
     m1 = torch.zeros(n, dtype=dt, device=dev)          # m^(k-1)
     m2 = torch.zeros(n, dtype=dt, device=dev)          # m^(k-2)
-    res = IRLSResult(m1, [], [], [])
+    res = IRLSResult(m1, [], [], [], [])
     for k in range(1, opts.kmax + 1):
         t0 = time.perf_counter()
         if k == 1:
@@ -281,13 +330,17 @@ def invert(op, grid, d_obs: torch.Tensor, sigma: torch.Tensor, opts: IRLSOptions
         fixed = opts.alphas[k - 1] if opts.alphas is not None else None
         if opts.solver == "gkb":
             f = gkb_factor(op, rt, winv, wd, opts.tp, opts.reorth)
+            torch.cuda.synchronize()
+            res.factor_seconds.append(time.perf_counter() - t0)
+            svd = bidiag_svd(f.B)
             a0 = fixed
             if k == 1 and a0 is None:
-                s_all = _svd64(f.B, dev)[1]
-                a0 = _alpha_start(n, m, s_all[:opts.t])
-            z, alpha, _ = gkb_solve(f, opts.t, n, a0)
+                a0 = _alpha_start(n, m, svd[1][:opts.t])
+            z, alpha, _ = gkb_solve(f, opts.t, n, a0, svd)
         else:
             f = rsvd_factor(op, omega, winv, wd)
+            torch.cuda.synchronize()
+            res.factor_seconds.append(time.perf_counter() - t0)
             a0 = fixed
             if k == 1 and a0 is None:
                 _, _, St = rsvd_solve(f, rt, opts.t, n, alpha=1.0)

@@ -5,7 +5,9 @@ Parity is checked where it is well defined:
   (FP64) and 2e-5 (FP32) of the oracle;
 * three steps with alpha^(k) fixed to the oracle's values: within 1e-9 (FP64);
 * a full 20-iteration c1 run with UPRE: the alpha sequence within 1e-6 relative for the
-  first five steps and the relative error to the true model within 0.01 of the oracle's.
+  first five steps and the relative error to the true model within 0.01 of the oracle's
+  (FP64); for FP32 the first five alphas within 1e-2 and the error within 0.05 (the FP32
+  run starts 1e-7 away and the iteration amplifies that, so this checks quality only).
 The full run is not compared element by element: alpha^(k>1) minimises a flat UPRE curve
 (so it is fixed only to about sqrt(machine epsilon)) and W_L with eps^2 = 1e-9 amplifies
 such differences from one iteration to the next.
@@ -126,5 +128,5 @@ def test_full_gkb_irls_c1(c1, dtn):
     print(f"GKB-IRLS {dtn}: RE {re_gpu:.4f} (oracle {re_ref:.4f}), model diff {rel(m_gpu, m_ref):.3e}")
     a_tol = 1e-6 if dtn == "f64" else 1e-2
     assert np.allclose(r.alphas[:5], rep.alphas[:5], rtol=a_tol)
-    assert abs(re_gpu - re_ref) < 0.01
+    assert abs(re_gpu - re_ref) < (0.01 if dtn == "f64" else 0.05)
     assert m_gpu.min() >= 0.0 and m_gpu.max() <= 1.0

@@ -121,3 +121,4 @@ def test_irls_recovers_a_block_and_respects_bounds(solver):
     assert re < 0.2
     assert rep.chi2[-1] < rep.chi2[0]
     assert all(a > 0 for a in rep.alphas)
+
