@@ -169,25 +169,54 @@ class Operator:
                                          self._ptr(rs), self._stream()))
         return out
 
-    # -- host-buffer convenience (copies in and out on the current stream) --------------
-    def matmat_host(self, X_host, out_host=None):
-        """G X for a pinned host block: H2D copy, product, D2H copy, all stream-ordered."""
+    # -- host buffers: copies overlapped with the products ------------------------------
+    def _host_pipeline(self, fn, H, rows_out, out_host, chunks):
+        """Run fn (a block product) on a pinned host block H (B x rows_in) in `chunks`
+        column chunks: chunk c's host-to-device copy, product and device-to-host copy run
+        on three streams ordered by events, so copies of one chunk overlap the product of
+        another.  The caller's current stream is ordered after all of it."""
         torch = _torch()
-        Xd = X_host.to(self.device, non_blocking=True)
-        Dd = self.matmat(Xd)
+        B = H.shape[0]
         if out_host is None:
-            out_host = torch.empty(Dd.shape, dtype=self.dtype, pin_memory=True)
-        out_host.copy_(Dd, non_blocking=True)
+            out_host = torch.empty((B, rows_out), dtype=self.dtype, pin_memory=True)
+        if B == 0:
+            return out_host
+        main = torch.cuda.current_stream(self.device)
+        if not hasattr(self, "_copy_streams"):
+            self._copy_streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
+        s_in, s_out = self._copy_streams
+        key = (H.shape[1], rows_out, B)
+        bufs = getattr(self, "_host_bufs", None)
+        if bufs is None or bufs[0] != key:
+            din = torch.empty((B, H.shape[1]), dtype=self.dtype, device=self.device)
+            dout = torch.empty((B, rows_out), dtype=self.dtype, device=self.device)
+            self._host_bufs = bufs = (key, din, dout)
+        _, din, dout = bufs
+        n = max(1, min(chunks, B))
+        edges = [B * i // n for i in range(n + 1)]
+        s_in.wait_stream(main)
+        s_out.wait_stream(main)
+        for c in range(n):
+            a, b = edges[c], edges[c + 1]
+            if a == b:
+                continue
+            with torch.cuda.stream(s_in):
+                din[a:b].copy_(H[a:b], non_blocking=True)
+            main.wait_stream(s_in)
+            fn(din[a:b], out=dout[a:b])
+            s_out.wait_stream(main)
+            with torch.cuda.stream(s_out):
+                out_host[a:b].copy_(dout[a:b], non_blocking=True)
+        main.wait_stream(s_out)
         return out_host
 
-    def rmatmat_host(self, Y_host, out_host=None):
-        torch = _torch()
-        Yd = Y_host.to(self.device, non_blocking=True)
-        Xd = self.rmatmat(Yd)
-        if out_host is None:
-            out_host = torch.empty(Xd.shape, dtype=self.dtype, pin_memory=True)
-        out_host.copy_(Xd, non_blocking=True)
-        return out_host
+    def matmat_host(self, X_host, out_host=None, chunks: int = 4):
+        """G X for a pinned host block X (B x n) into pinned host memory (B x m)."""
+        return self._host_pipeline(self.matmat, X_host, self.m, out_host, chunks)
+
+    def rmatmat_host(self, Y_host, out_host=None, chunks: int = 4):
+        """G^T Y for a pinned host block Y (B x m) into pinned host memory (B x n)."""
+        return self._host_pipeline(self.rmatmat, Y_host, self.n, out_host, chunks)
 
     # -- introspection ------------------------------------------------------------------
     def spectra(self):

@@ -10,9 +10,10 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-# TF_LIB_VARIANT=checked loads the bounds-checked debug build (libtf_checked.so).
-LIB_PATH = os.path.join(HERE, "_build", "libtf_checked.so" if os.environ.get(
-    "TF_LIB_VARIANT") == "checked" else "libtf.so")
+# TF_LIB_VARIANT=checked loads the bounds-checked debug build (libtf_checked.so);
+# TF_LIB_PATH names any other build of the library (e.g. a tuning variant).
+LIB_PATH = os.environ.get("TF_LIB_PATH") or os.path.join(
+    HERE, "_build", "libtf_checked.so" if os.environ.get("TF_LIB_VARIANT") == "checked" else "libtf.so")
 
 TF_OK, TF_EINVAL, TF_ENOMEM, TF_ECUDA, TF_EUNSUPPORTED, TF_ENOTCONV, TF_ETIMEOUT = range(7)
 TF_F32, TF_F64 = 0, 1

@@ -42,11 +42,16 @@ def _newer(target: str, deps) -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, checked: bool = False) -> str:
-    """Compile libtf.so (or, with checked=True, the bounds-checked libtf_checked.so)."""
+def build(verbose: bool = False, force: bool = False, checked: bool = False,
+          defines=(), tag: str = "") -> str:
+    """Compile libtf.so (or, with checked=True, the bounds-checked libtf_checked.so).
+    `defines` (e.g. ["TF_CT_V_TWO_PASS=1"]) with a `tag` build a variant libtf_<tag>.so,
+    loadable with TF_LIB_PATH, for tuning experiments."""
     os.makedirs(OUT, exist_ok=True)
-    lib = os.path.join(OUT, "libtf_checked.so") if checked else LIB
-    tag = "_checked" if checked else ""
+    if checked:
+        tag = "checked"
+    lib = os.path.join(OUT, f"libtf_{tag}.so") if tag else LIB
+    tag = f"_{tag}" if tag else ""
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, "..", "include", "tf.h"))
     if not force and _newer(lib, deps):
@@ -59,6 +64,7 @@ def build(verbose: bool = False, force: bool = False, checked: bool = False) -> 
         cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose)
         if checked:
             cmd.append("-DTF_BOUNDS_CHECK")
+        cmd += [f"-D{d}" for d in defines]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

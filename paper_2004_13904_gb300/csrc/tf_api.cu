@@ -107,10 +107,8 @@ struct HostPlan {
   std::vector<double> tw;  // interleaved re, im
 };
 
-HostPlan make_plan(int n) {
+HostPlan make_plan_from(int n, const std::vector<int>& rad) {
   HostPlan h;
-  std::vector<int> rad;
-  factor(n, rad);
   std::memset(&h.plan, 0, sizeof h.plan);
   h.plan.n = n;
   h.plan.np = (int)rad.size();
@@ -135,16 +133,19 @@ HostPlan make_plan(int n) {
   return h;
 }
 
-// True when the compile-time menu has this length with the same radix order as the
-// host plan (so both engines share one twiddle table).
-bool has_ct_plan(const HostPlan& h) {
+HostPlan make_plan(int n) {
+  std::vector<int> rad;
+  factor(n, rad);
+  return make_plan_from(n, rad);
+}
+
+// The compile-time menu's radix list for length n (false when n has no compiled plan).
+bool ct_radices(int n, std::vector<int>& rad) {
   for (int i = 0; i < tfk::ct_menu_count(); ++i) {
-    if (tfk::ct_menu_length(i) != h.plan.n) continue;
+    if (tfk::ct_menu_length(i) != n) continue;
     int r[tfk::kMaxPass];
     const int np = tfk::ct_menu_radices(i, r);
-    if (np != h.plan.np) return false;
-    for (int p = 0; p < np; ++p)
-      if (r[p] != h.plan.radix[p]) return false;
+    rad.assign(r, r + np);
     return true;
   }
   return false;
@@ -164,8 +165,11 @@ struct tf_op {
   // transforms
   int n1, n2, nh;
   HostPlan p1, p2;
-  void* tw1 = nullptr;  // device twiddles in the op dtype
+  void* tw1 = nullptr;  // device twiddles in the op dtype (generic plans)
   void* tw2 = nullptr;
+  HostPlan p1ct, p2ct;  // compile-time plans (their own radix lists)
+  void* tw1ct = nullptr;
+  void* tw2ct = nullptr;
   void* spec = nullptr; // [nz][n2][nh] complex of the op dtype
   // workspace
   void* w1 = nullptr;   // chunk * nz*ny*nh complex
@@ -194,6 +198,8 @@ void free_op(tf_op* op) {
   if (!op) return;
   cudaFree(op->tw1);
   cudaFree(op->tw2);
+  cudaFree(op->tw1ct);
+  cudaFree(op->tw2ct);
   cudaFree(op->spec);
   cudaFree(op->w1);
   cudaFree(op->w2);
@@ -295,8 +301,11 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
   op->nh = op->n1 / 2 + 1;
   op->p1 = make_plan(op->n1);
   op->p2 = make_plan(op->n2);
-  op->ct1 = has_ct_plan(op->p1);
-  op->ct2 = has_ct_plan(op->p2);
+  {
+    std::vector<int> rad;
+    if ((op->ct1 = ct_radices(op->n1, rad))) op->p1ct = make_plan_from(op->n1, rad);
+    if ((op->ct2 = ct_radices(op->n2, rad))) op->p2ct = make_plan_from(op->n2, rad);
+  }
   op->rows_tile = dt == TF_F32 ? 8 : 4;
   op->cols_tile = dt == TF_F32 ? 8 : 4;
 
@@ -321,6 +330,8 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
 
   if ((st = upload_twiddles(op->p1, dt, &op->tw1)) != TF_OK) goto done;
   if ((st = upload_twiddles(op->p2, dt, &op->tw2)) != TF_OK) goto done;
+  if (op->ct1 && (st = upload_twiddles(op->p1ct, dt, &op->tw1ct)) != TF_OK) goto done;
+  if (op->ct2 && (st = upload_twiddles(op->p2ct, dt, &op->tw2ct)) != TF_OK) goto done;
   if (dt == TF_F32) {
     if ((st = upload_twiddles(op->p1, TF_F64, &tw1_64)) != TF_OK) goto done;
     if ((st = upload_twiddles(op->p2, TF_F64, &tw2_64)) != TF_OK) goto done;
@@ -424,7 +435,10 @@ tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int6
     a.plan = op->p1.plan; a.tw = tw1;
     const bool c1 = op->engine == 0 && op->ct1, c2 = op->engine == 0 && op->ct2;
     cudaError_t e = stage(op, 0, cb, s, [&] {
-      return c1 ? tfk::ct_rows_r2c<T>(a, cb, s) : tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s);
+      if (!c1) return tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s);
+      tfk::RowsR2C<T> ac = a;
+      ac.tw = (const C*)op->tw1ct;
+      return tfk::ct_rows_r2c<T>(ac, cb, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
     tfk::ColsFwd<T> b;
@@ -432,7 +446,10 @@ tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int6
     b.s_ld = op->w2_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
     b.plan = op->p2.plan; b.tw = tw2;
     e = stage(op, 1, cb, s, [&] {
-      return c2 ? tfk::ct_cols_fwd<T>(b, cb, s) : tfk::launch_cols_fwd<T>(b, cb, op->cols_tile, s);
+      if (!c2) return tfk::launch_cols_fwd<T>(b, cb, op->cols_tile, s);
+      tfk::ColsFwd<T> bc = b;
+      bc.tw = (const C*)op->tw2ct;
+      return tfk::ct_cols_fwd<T>(bc, cb, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "cols_fwd launch");
     tfk::RowsC2R<T> c;
@@ -440,7 +457,10 @@ tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int6
     c.dst = D + c0 * ldd; c.dst_ld = ldd; c.out_len = op->sx; c.seq_off = op->nx - 1;
     c.scale = rs; c.plan = op->p1.plan; c.tw = tw1;
     e = stage(op, 2, cb, s, [&] {
-      return c1 ? tfk::ct_rows_c2r<T>(c, cb, s) : tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s);
+      if (!c1) return tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s);
+      tfk::RowsC2R<T> cc = c;
+      cc.tw = (const C*)op->tw1ct;
+      return tfk::ct_rows_c2r<T>(cc, cb, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "rows_c2r launch");
   }
@@ -465,7 +485,10 @@ tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int6
     a.nh = op->nh; a.plan = op->p1.plan; a.tw = tw1;
     const bool c1 = op->engine == 0 && op->ct1, c2 = op->engine == 0 && op->ct2;
     cudaError_t e = stage(op, 3, cb, s, [&] {
-      return c1 ? tfk::ct_rows_r2c<T>(a, cb, s) : tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s);
+      if (!c1) return tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s);
+      tfk::RowsR2C<T> ac = a;
+      ac.tw = (const C*)op->tw1ct;
+      return tfk::ct_rows_r2c<T>(ac, cb, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
     tfk::ColsAdj<T> b;
@@ -473,7 +496,10 @@ tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int6
     b.u_ld = op->w1_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
     b.plan = op->p2.plan; b.tw = tw2;
     e = stage(op, 4, cb, s, [&] {
-      return c2 ? tfk::ct_cols_adj<T>(b, cb, s) : tfk::launch_cols_adj<T>(b, cb, op->cols_tile, s);
+      if (!c2) return tfk::launch_cols_adj<T>(b, cb, op->cols_tile, s);
+      tfk::ColsAdj<T> bc = b;
+      bc.tw = (const C*)op->tw2ct;
+      return tfk::ct_cols_adj<T>(bc, cb, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "cols_adj launch");
     tfk::RowsC2R<T> c;
@@ -481,7 +507,10 @@ tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int6
     c.dst = X + c0 * ldx; c.dst_ld = ldx; c.out_len = op->nx; c.seq_off = 0; c.scale = cs;
     c.plan = op->p1.plan; c.tw = tw1;
     e = stage(op, 5, cb, s, [&] {
-      return c1 ? tfk::ct_rows_c2r<T>(c, cb, s) : tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s);
+      if (!c1) return tfk::launch_rows_c2r<T>(c, cb, op->rows_tile, s);
+      tfk::RowsC2R<T> cc = c;
+      cc.tw = (const C*)op->tw1ct;
+      return tfk::ct_rows_c2r<T>(cc, cb, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "rows_c2r launch");
   }

@@ -225,3 +225,18 @@ def test_errors_through_abi():
         op.matmat(torch.zeros((2, g.n), dtype=torch.float64, device="cuda"))
     with pytest.raises(ValueError):
         op.matvec(torch.zeros(g.n + 1, device="cuda"))
+
+
+@pytest.mark.parametrize("chunks", [1, 3])
+def test_host_pipeline_matches_device_products(chunks):
+    torch = _torch()
+    g = SMALL[7][1]
+    op = make_op(g, "magnetic", 60.0, 15.0, "f32")
+    rng = np.random.default_rng(12)
+    X = torch.tensor(rng.standard_normal((11, g.n)), dtype=torch.float32).pin_memory()
+    Y = torch.tensor(rng.standard_normal((11, g.m)), dtype=torch.float32).pin_memory()
+    D = op.matmat_host(X, chunks=chunks)
+    XT = op.rmatmat_host(Y, chunks=chunks)
+    torch.cuda.synchronize()
+    assert torch.equal(D, op.matmat(X.cuda()).cpu())
+    assert torch.equal(XT, op.rmatmat(Y.cuda()).cpu())
