@@ -4,6 +4,7 @@
 // index arithmetic is resolved at compile time.  Included by tf_ct_f32.cu / tf_ct_f64.cu.
 #pragma once
 #include <atomic>
+#include <type_traits>
 
 #include "tf_check.cuh"
 #include "tf_fft_ct.cuh"
@@ -32,6 +33,17 @@ using ct::Vec;
 __host__ __device__ constexpr int twpad(int c) { return (c + 1) & ~1; }
 
 template <typename C> __device__ __forceinline__ C zero() { return mk<C>(0, 0); }
+
+// Register budgets of the column kernels, as a minimum number of resident CTAs per SM
+// for __launch_bounds__ (measured with 1260-column blocks at transform lengths 64 to
+// 512: the single-precision forward kernel is fastest near 128 registers a thread, the
+// adjoint near 100; the double kernels are indifferent).  The row kernels keep the compiler's
+// default budget, which measured fastest for them.
+template <typename T> constexpr int cols_min_blocks(int nt, int threads_per_sm) {
+  return std::is_same<T, float>::value && threads_per_sm / nt > 1 ? threads_per_sm / nt : 1;
+}
+template <typename T> constexpr int kFwdThreadsPerSM = 512;
+template <typename T> constexpr int kAdjThreadsPerSM = 640;
 
 template <typename T, class P, int TB, int V, int NT>
 __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
@@ -130,10 +142,21 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
   }
 }
 
+// Spectrum values are staged in registers ahead of use in single precision only (the
+// double kernels measured no gain from it).
+template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::value;
+
+// Column stage of G x.  In single precision each thread loads the spectrum values that
+// its last forward pass multiplies at the start of every layer, into registers, so that
+// their global-memory latency overlaps the layer's first passes.
 template <typename T, class P, int TB, int V, int NT>
-__global__ void __launch_bounds__(NT) k_cols_fwd(const ColsFwd<T> a) {
+__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>)) k_cols_fwd(const ColsFwd<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n;
+  constexpr bool kPre = kSpecPrefetch<T>;
+  constexpr int RL = P::last_r, NSL = P::last_ns;
+  typedef ct::PassMap<RL, NSL, N, TB, V> LM;
+  constexpr int ITL = kPre ? (LM::TOTAL + NT - 1) / NT : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
@@ -145,8 +168,24 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const ColsFwd<T> a) {
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
   const int z_ext = a.nz * ny * nh, g_ext = a.nz * N * nh, s_ext = sy * nh;
   const C* spec = a.spec;
+  C gpre[kPre ? ITL * RL : 1][V];
   for (int r = 0; r < a.nz; ++r) {
     const int zoff = r * ny * nh, goff = r * N * nh;
+#pragma unroll
+    for (int it = 0; it < ITL; ++it) {
+      const int u = threadIdx.x + it * NT;
+      int b0 = 0;
+      const int base = LM::first_idx(u < LM::TOTAL ? u : 0, b0);
+#pragma unroll
+      for (int rr = 0; rr < RL; ++rr)
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          const int k1 = k0 + b0 + q;
+          const int e = goff + (base + rr * NSL) * nh + k1;
+          gpre[it * RL + rr][q] = zero<C>();
+          if (u < LM::TOTAL && k1 < nh && TF_IN(kSiteFwdSpec, e, g_ext)) gpre[it * RL + rr][q] = spec[e];
+        }
+    }
     const bool first_layer = (r == 0);
     auto load = [=](int idx, int b0, C* o) {
 #pragma unroll
@@ -157,16 +196,21 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const ColsFwd<T> a) {
         if (idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e, z_ext)) o[q] = z[e];
       }
     };
-    auto mac = [=](int idx, int b0, const C* v, int) {
+    auto mac = [&](int idx, int b0, const C* v, int slot) {
       C cur[V];
       const bool acc_ok = TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB);
       if (!first_layer && acc_ok) Vec<V, C>::ld(acc + idx * TB + b0, cur);
 #pragma unroll
       for (int q = 0; q < V; ++q) {
-        const int k1 = k0 + b0 + q;
-        const int e = goff + idx * nh + k1;
-        C g = zero<C>();
-        if (k1 < nh && TF_IN(kSiteFwdSpec, e, g_ext)) g = spec[e];
+        C g;
+        if constexpr (kPre) {
+          g = gpre[slot][q];
+        } else {
+          const int k1 = k0 + b0 + q;
+          const int e = goff + idx * nh + k1;
+          g = zero<C>();
+          if (k1 < nh && TF_IN(kSiteFwdSpec, e, g_ext)) g = spec[e];
+        }
         const C p = cmul(g, v[q]);
         cur[q] = first_layer ? p : cadd(cur[q], p);
       }
@@ -190,8 +234,10 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const ColsFwd<T> a) {
   P::template run<TB, V, NT, true>(tw, buf, lacc, store);
 }
 
+// Column stage of G^T y: forward transform of the data columns into shared memory, then
+// per layer the product with conj(G_r) and the inverse transform.
 template <typename T, class P, int TB, int V, int NT>
-__global__ void __launch_bounds__(NT) k_cols_adj(const ColsAdj<T> a) {
+__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kAdjThreadsPerSM<T>)) k_cols_adj(const ColsAdj<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -204,7 +250,6 @@ __global__ void __launch_bounds__(NT) k_cols_adj(const ColsAdj<T> a) {
   const int nh = a.nh, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
   const int z_ext = sy * nh, g_ext = a.nz * N * nh, u_ext = a.nz * ny * nh;
-  const C* spec = a.spec;
   auto load = [=](int idx, int b0, C* o) {
     const int j = idx - (ny - 1);
 #pragma unroll
@@ -219,6 +264,7 @@ __global__ void __launch_bounds__(NT) k_cols_adj(const ColsAdj<T> a) {
   };
   P::template run<TB, V, NT, false>(tw, buf, load, sacc);
   C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
+  const C* spec = a.spec;
   for (int r = 0; r < a.nz; ++r) {
     const int goff = r * N * nh, uoff = r * ny * nh;
     auto prod = [=](int idx, int b0, C* o) {

@@ -78,8 +78,21 @@ template <typename C, int TB, int V> struct Buf {
 template <class T, class = void> struct IsBuf : std::false_type {};
 template <class T> struct IsBuf<T, std::void_t<decltype(T::kIsBuf)>> : std::true_type {};
 
+// The task -> (output index, sequence) mapping of a pass, as the pass computes it: task
+// u writes first_idx(u) + r * Ns, r < R, for sequences b0 .. b0 + V - 1.
+template <int R, int Ns, int N, int TB, int V> struct PassMap {
+  static constexpr int NB = N / R, G = TB / V, TOTAL = NB * G;
+  __device__ __forceinline__ static int first_idx(int u, int& b0) {
+    const int j = u / G;
+    b0 = (u % G) * V;
+    const int k = j % Ns;
+    return (j - k) * R + k;
+  }
+};
+
 // One radix-R pass with stride Ns over TB sequences, V per thread, NT threads.
-// Loader: ld(idx, b0, C out[V]); storer: st(idx, b0, const C in[V], 0).
+// Loader: ld(idx, b0, C out[V]); storer: st(idx, b0, const C in[V], slot) where slot =
+// it * R + r numbers the thread's outputs of the pass (a compile-time constant).
 template <int R, int Ns, int N, int TB, int V, int NT, bool INV, typename C, class L, class S>
 __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, const S& st) {
   constexpr int NB = N / R;
@@ -121,15 +134,14 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
   for (int it = 0; it < ITER; ++it) {
     const int u = threadIdx.x + it * NT;
     if (TOTAL % NT == 0 || u < TOTAL) {
-      const int j = u / G, b0 = (u % G) * V;
-      const int k = j % Ns;
-      const int base = (j - k) * R + k;
+      int b0;
+      const int base = PassMap<R, Ns, N, TB, V>::first_idx(u, b0);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         C t[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) t[q] = v[it][q][r];
-        st(base + r * Ns, b0, t, 0);
+        st(base + r * Ns, b0, t, it * R + r);
       }
     }
   }
@@ -154,8 +166,17 @@ template <int N, int Ns, int TwOff, int R, int... Rest> struct Run<N, Ns, TwOff,
   }
 };
 
+template <int... Rs> struct LastOf;
+template <int R> struct LastOf<R> { static constexpr int r = R, prod_before = 1; };
+template <int R, int... Rest> struct LastOf<R, Rest...> {
+  static constexpr int r = LastOf<Rest...>::r;
+  static constexpr int prod_before = R * LastOf<Rest...>::prod_before;
+};
+
 template <int N, int... Rs> struct Plan {
   static constexpr int n = N;
+  static constexpr int last_r = LastOf<Rs...>::r;          // radix of the last pass
+  static constexpr int last_ns = LastOf<Rs...>::prod_before;  // its stride
   template <int TB, int V, int NT, bool INV, typename C, class L0, class SL>
   static __device__ __forceinline__ void run(const C* tw, C* buf, const L0& first, const SL& last) {
     Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true>(tw, buf, first, last);
