@@ -45,10 +45,13 @@ template <typename T> constexpr int cols_min_blocks(int nt, int threads_per_sm) 
 template <typename T> constexpr int kFwdThreadsPerSM = 512;
 template <typename T> constexpr int kAdjThreadsPerSM = 640;
 
+// The row kernels stage and unpack two adjacent sequences (2q, 2q + 1) per thread and
+// element: one 16-byte shared-memory access (the pair is adjacent in the swizzled
+// buffer), and the four real rows 2 (pair0 + 2q) + 0..3 that feed them.
 template <typename T, class P, int TB, int V, int NT>
 __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
   typedef typename CT<T>::C C;
-  constexpr int N = P::n, NH = N / 2 + 1;
+  constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
@@ -58,48 +61,54 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
   const int len = a.row_len, off = a.seq_off, nrows = a.nrows;
   const int src_ext = nrows * len;
   const T* scale = a.scale;
-  for (int u = threadIdx.x; u < TB * N; u += NT) {
-    const int pp = u / N, n = u - pp * N;
-    const int ra = 2 * (pair0 + pp), rb = ra + 1;
+  for (int u = threadIdx.x; u < TP * N; u += NT) {
+    const int q = u / N, n = u - q * N;
+    const int r0 = 2 * (pair0 + 2 * q);
     const int e = n - off;
-    T xa = T(0), xb = T(0);
+    T x[4] = {T(0), T(0), T(0), T(0)};
     if (e >= 0 && e < len) {
-      if (ra < nrows) {
-        const int o = ra * len + e;
-        if (TF_IN(kSiteR2cSrc, o, src_ext)) xa = src[o];
-        if (scale && TF_IN(kSiteR2cScale, o, src_ext)) xa *= scale[o];
-      }
-      if (rb < nrows) {
-        const int o = rb * len + e;
-        if (TF_IN(kSiteR2cSrc, o, src_ext)) xb = src[o];
-        if (scale && TF_IN(kSiteR2cScale, o, src_ext)) xb *= scale[o];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (r0 + i >= nrows) break;
+        const int o = (r0 + i) * len + e;
+        if (TF_IN(kSiteR2cSrc, o, src_ext)) x[i] = src[o];
+        if (scale && TF_IN(kSiteR2cScale, o, src_ext)) x[i] *= scale[o];
       }
     }
-    buf[ct::at<C, TB>(n, pp)] = mk<C>(xa, xb);
+    const C v[2] = {mk<C>(x[0], x[1]), mk<C>(x[2], x[3])};
+    const int p = ct::at<C, TB>(n, 2 * q);
+    if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::st(buf + p, v);
   }
   __syncthreads();
   const ct::Buf<C, TB, V> b{buf, N * TB};
   P::template run<TB, V, NT, false>(tw, buf, b, b);
   C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int dst_ext = nrows * NH;
-  for (int u = threadIdx.x; u < TB * NH; u += NT) {
-    const int pp = u / NH, k = u - pp * NH;
-    const int ra = 2 * (pair0 + pp), rb = ra + 1;
-    if (ra >= nrows) continue;
-    const C z = buf[ct::at<C, TB>(k, pp)];
-    C zc = buf[ct::at<C, TB>(k ? N - k : 0, pp)];
-    zc.y = -zc.y;
-    if (TF_IN(kSiteR2cDst, ra * NH + k, dst_ext))
-      dst[ra * NH + k] = mk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
-    if (rb < nrows && TF_IN(kSiteR2cDst, rb * NH + k, dst_ext))
-      dst[rb * NH + k] = mk<C>(T(0.5) * (z.y - zc.y), T(-0.5) * (z.x - zc.x));
+  for (int u = threadIdx.x; u < TP * NH; u += NT) {
+    const int q = u / NH, k = u - q * NH;
+    const int r0 = 2 * (pair0 + 2 * q);
+    if (r0 >= nrows) continue;
+    C z[2], zc[2];
+    const int pk = ct::at<C, TB>(k, 2 * q), pc = ct::at<C, TB>(k ? N - k : 0, 2 * q);
+    if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::ld(buf + pk, z);
+    if (TF_IN(kSiteSmem + 3, pc + 1, N * TB)) Vec<2, C>::ld(buf + pc, zc);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ra = r0 + 2 * h, rb = ra + 1;
+      if (ra >= nrows) break;
+      zc[h].y = -zc[h].y;
+      if (TF_IN(kSiteR2cDst, ra * NH + k, dst_ext))
+        dst[ra * NH + k] = mk<C>(T(0.5) * (z[h].x + zc[h].x), T(0.5) * (z[h].y + zc[h].y));
+      if (rb < nrows && TF_IN(kSiteR2cDst, rb * NH + k, dst_ext))
+        dst[rb * NH + k] = mk<C>(T(0.5) * (z[h].y - zc[h].y), T(-0.5) * (z[h].x - zc[h].x));
+    }
   }
 }
 
 template <typename T, class P, int TB, int V, int NT>
 __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
   typedef typename CT<T>::C C;
-  constexpr int N = P::n, NH = N / 2 + 1;
+  constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
@@ -108,16 +117,30 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
   const int nrows = a.nrows;
   const C* src = a.src + (int64_t)blockIdx.y * a.src_ld;
   const int src_ext = nrows * NH;
-  for (int u = threadIdx.x; u < TB * NH; u += NT) {
-    const int pp = u / NH, k = u - pp * NH;
-    const int ra = 2 * (pair0 + pp), rb = ra + 1;
-    C xa = zero<C>(), xb = zero<C>();
-    if (ra < nrows && TF_IN(kSiteC2rSrc, ra * NH + k, src_ext)) xa = src[ra * NH + k];
-    if (rb < nrows && TF_IN(kSiteC2rSrc, rb * NH + k, src_ext)) xb = src[rb * NH + k];
+  for (int u = threadIdx.x; u < TP * NH; u += NT) {
+    const int q = u / NH, k = u - q * NH;
+    const int r0 = 2 * (pair0 + 2 * q);
+    C x[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[i] = zero<C>();
+      if (r0 + i < nrows && TF_IN(kSiteC2rSrc, (r0 + i) * NH + k, src_ext)) x[i] = src[(r0 + i) * NH + k];
+    }
     const bool self = (k == 0) || (2 * k == N);
-    if (self) { xa.y = T(0); xb.y = T(0); }
-    buf[ct::at<C, TB>(k, pp)] = mk<C>(xa.x - xb.y, xa.y + xb.x);
-    if (!self) buf[ct::at<C, TB>(N - k, pp)] = mk<C>(xa.x + xb.y, xb.x - xa.y);
+    C lo[2], hi[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      C xa = x[2 * h], xb = x[2 * h + 1];
+      if (self) { xa.y = T(0); xb.y = T(0); }
+      lo[h] = mk<C>(xa.x - xb.y, xa.y + xb.x);
+      hi[h] = mk<C>(xa.x + xb.y, xb.x - xa.y);
+    }
+    const int pk = ct::at<C, TB>(k, 2 * q);
+    if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::st(buf + pk, lo);
+    if (!self) {
+      const int pc = ct::at<C, TB>(N - k, 2 * q);
+      if (TF_IN(kSiteSmem + 3, pc + 1, N * TB)) Vec<2, C>::st(buf + pc, hi);
+    }
   }
   __syncthreads();
   const ct::Buf<C, TB, V> b{buf, N * TB};
@@ -126,18 +149,20 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
   const int L = a.out_len, off = a.seq_off;
   const int dst_ext = nrows * L;
   const T* scale = a.scale;
-  for (int u = threadIdx.x; u < TB * L; u += NT) {
-    const int pp = u / L, i = u - pp * L;
-    const int ra = 2 * (pair0 + pp), rb = ra + 1;
-    if (ra >= nrows) continue;
-    const C z = buf[ct::at<C, TB>(off + i, pp)];
-    const int oa = ra * L + i;
-    if (TF_IN(kSiteC2rDst, oa, dst_ext))
-      dst[oa] = (scale && TF_IN(kSiteC2rScale, oa, dst_ext)) ? z.x * scale[oa] : z.x;
-    if (rb < nrows) {
-      const int ob = rb * L + i;
-      if (TF_IN(kSiteC2rDst, ob, dst_ext))
-        dst[ob] = (scale && TF_IN(kSiteC2rScale, ob, dst_ext)) ? z.y * scale[ob] : z.y;
+  for (int u = threadIdx.x; u < TP * L; u += NT) {
+    const int q = u / L, i = u - q * L;
+    const int r0 = 2 * (pair0 + 2 * q);
+    if (r0 >= nrows) continue;
+    C z[2];
+    const int p = ct::at<C, TB>(off + i, 2 * q);
+    if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::ld(buf + p, z);
+    const T y[4] = {z[0].x, z[0].y, z[1].x, z[1].y};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (r0 + j >= nrows) break;
+      const int o = (r0 + j) * L + i;
+      if (TF_IN(kSiteC2rDst, o, dst_ext))
+        dst[o] = (scale && TF_IN(kSiteC2rScale, o, dst_ext)) ? y[j] * scale[o] : y[j];
     }
   }
 }

@@ -49,15 +49,23 @@ template <> struct Vec<4, float2> {
 };
 
 // Position of sequence b at element idx in the [N][TB] working buffer.  The sequence
-// index is XOR-swizzled by an even function of idx, so that walking idx at fixed b (the
-// staging and unpacking phases) spreads over the shared-memory banks instead of hitting
-// one bank group, while pairs (2k, 2k+1) stay adjacent for 16-byte accesses.
-template <typename C, int TB> __host__ __device__ constexpr int swz(int idx) {
+// index is XOR-swizzled by an even function of the row, so that walking idx at fixed b
+// (the staging and unpacking phases) spreads over the shared-memory banks instead of
+// hitting one bank group, while pairs (2k, 2k+1) stay adjacent for 16-byte accesses.
+template <typename C, int TB> __host__ __device__ constexpr int swz(int row) {
   constexpr int rows_per_line = (int)(128 / (TB * sizeof(C))) > 1 ? (int)(128 / (TB * sizeof(C))) : 1;
-  return TB >= 4 ? ((idx / rows_per_line) & (TB / 2 - 1)) << 1 : 0;
+  return TB >= 4 ? ((row / rows_per_line) & (TB / 2 - 1)) << 1 : 0;
 }
-template <typename C, int TB> __device__ __forceinline__ int at(int idx, int b) {
-  return idx * TB + (b ^ swz<C, TB>(idx));
+// Rows of 64 bytes fill half of the 32 banks, the half given by the row's parity.  The
+// first pass of every plan is radix 8 and stores rows idx and idx + 8 in the same
+// quarter-warp phase; swapping the rows of each even/odd pair in every other block of 8
+// puts those two in different halves.  (A permutation of [0, N) for even N.)
+template <typename C, int TB> __host__ __device__ constexpr int row_of(int idx) {
+  return TB * sizeof(C) == 64 ? idx ^ ((idx >> 3) & 1) : idx;
+}
+template <typename C, int TB> __host__ __device__ __forceinline__ int at(int idx, int b) {
+  const int row = row_of<C, TB>(idx);
+  return row * TB + (b ^ swz<C, TB>(row));
 }
 
 // The working buffer: [N][TB] complex, sequence index fastest (swizzled).
