@@ -164,16 +164,17 @@ struct tf_op {
   int device;
   // transforms
   int n1, n2, nh;
+  int hs;               // row stride of half-spectrum buffers: nh rounded up to 16
   HostPlan p1, p2;
   void* tw1 = nullptr;  // device twiddles in the op dtype (generic plans)
   void* tw2 = nullptr;
   HostPlan p1ct, p2ct;  // compile-time plans (their own radix lists)
   void* tw1ct = nullptr;
   void* tw2ct = nullptr;
-  void* spec = nullptr; // [nz][n2][nh] complex of the op dtype
+  void* spec = nullptr; // [nz][n2][hs] complex of the op dtype
   // workspace
-  void* w1 = nullptr;   // chunk * nz*ny*nh complex
-  void* w2 = nullptr;   // chunk * sy*nh complex
+  void* w1 = nullptr;   // chunk * nz*ny*hs complex
+  void* w2 = nullptr;   // chunk * sy*hs complex
   int64_t chunk = 0;       // columns the allocated workspace holds
   int64_t chunk_cap = 0;   // most columns per chunk (grown into on demand)
   int rows_tile = 8, cols_tile = 8;
@@ -188,8 +189,8 @@ struct tf_op {
   size_t csize() const { return dtype == TF_F32 ? sizeof(float2) : sizeof(double2); }
   int64_t m() const { return (int64_t)sx * sy; }
   int64_t n() const { return (int64_t)nx * ny * nz; }
-  int64_t w1_per_col() const { return (int64_t)nz * ny * nh; }
-  int64_t w2_per_col() const { return (int64_t)sy * nh; }
+  int64_t w1_per_col() const { return (int64_t)nz * ny * hs; }
+  int64_t w2_per_col() const { return (int64_t)sy * hs; }
 };
 
 namespace {
@@ -225,14 +226,14 @@ tf_status upload_twiddles(const HostPlan& h, tf_dtype dt, void** dst) {
 }
 
 // Each workspace buffer carries a guard tail of one full transform column block
-// (n2 * nh complex values) beyond the last column it serves, so that no read near the
+// (n2 * hs complex values) beyond the last column it serves, so that no read near the
 // end of a column block can leave the allocation.
 tf_status alloc_workspace(tf_op* op, int64_t chunk) {
   cudaFree(op->w1);
   cudaFree(op->w2);
   op->w1 = op->w2 = nullptr;
   op->chunk = 0;
-  const size_t guard = (size_t)op->n2 * op->nh * op->csize();
+  const size_t guard = (size_t)op->n2 * op->hs * op->csize();
   cudaError_t e = cudaMalloc(&op->w1, (size_t)chunk * op->w1_per_col() * op->csize() + guard);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
   e = cudaMalloc(&op->w2, (size_t)chunk * op->w2_per_col() * op->csize() + guard);
@@ -299,6 +300,7 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
                 n2min, kMaxFft);
   }
   op->nh = op->n1 / 2 + 1;
+  op->hs = (op->nh + 15) & ~15;
   op->p1 = make_plan(op->n1);
   op->p2 = make_plan(op->n2);
   {
@@ -320,7 +322,7 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
   cudaError_t e;
   const int64_t ntab = (int64_t)op->nz * n2min * n1min;
   const int64_t nht = (int64_t)op->nz * n2min * op->nh;
-  const int64_t nspec = (int64_t)op->nz * op->n2 * op->nh;
+  const int64_t nspec = (int64_t)op->nz * op->n2 * op->hs;
 
 #define TF_TRY(call, what)                       \
   do {                                           \
@@ -345,6 +347,7 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
   TF_TRY(cudaMalloc(&d_tab, sizeof(double) * ntab), "cudaMalloc(kernel table)");
   TF_TRY(cudaMalloc(&d_ht, sizeof(double2) * nht), "cudaMalloc(row spectra)");
   TF_TRY(cudaMalloc(&d_spec64, sizeof(double2) * nspec), "cudaMalloc(spectra)");
+  TF_TRY(cudaMemsetAsync(d_spec64, 0, sizeof(double2) * nspec, s), "cudaMemsetAsync(spectra)");
   {
     tfk::TableArgs ta;
     ta.kind = kind; ta.n1min = n1min; ta.n2min = n2min; ta.nz = op->nz;
@@ -360,14 +363,14 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
 
     tfk::RowsR2C<double> ra;
     ra.src = d_tab; ra.src_ld = 0; ra.row_len = n1min; ra.nrows = op->nz * n2min;
-    ra.seq_off = 0; ra.scale = nullptr; ra.dst = d_ht; ra.dst_ld = 0; ra.nh = op->nh;
+    ra.seq_off = 0; ra.scale = nullptr; ra.dst = d_ht; ra.dst_ld = 0; ra.nh = op->nh; ra.hs = op->nh;
     ra.plan = op->p1.plan; ra.tw = (const double2*)tw1_64;
     TF_TRY(tfk::launch_rows_r2c<double>(ra, 1, 4, s), "row FFT of kernel table");
 
     tfk::SpecArgs sa;
     sa.ht = d_ht; sa.n2min = n2min; sa.nh = op->nh; sa.nz = op->nz;
     sa.scale = 1.0 / ((double)op->n1 * op->n2);
-    sa.spec = d_spec64; sa.plan = op->p2.plan; sa.tw = (const double2*)tw2_64;
+    sa.spec = d_spec64; sa.hs = op->hs; sa.plan = op->p2.plan; sa.tw = (const double2*)tw2_64;
     TF_TRY(tfk::launch_spectrum(sa, 4, s), "column FFT of kernel table");
   }
   if (dt == TF_F64) {
@@ -431,7 +434,7 @@ tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int6
     const int cb = (int)std::min<int64_t>(op->chunk, B - c0);
     tfk::RowsR2C<T> a;
     a.src = X + c0 * ldx; a.src_ld = ldx; a.row_len = op->nx; a.nrows = op->nz * op->ny;
-    a.seq_off = 0; a.scale = cs; a.dst = w1; a.dst_ld = op->w1_per_col(); a.nh = op->nh;
+    a.seq_off = 0; a.scale = cs; a.dst = w1; a.dst_ld = op->w1_per_col(); a.nh = op->nh; a.hs = op->hs;
     a.plan = op->p1.plan; a.tw = tw1;
     const bool c1 = op->engine == 0 && op->ct1, c2 = op->engine == 0 && op->ct2;
     cudaError_t e = stage(op, 0, cb, s, [&] {
@@ -443,7 +446,7 @@ tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int6
     if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
     tfk::ColsFwd<T> b;
     b.z = w1; b.z_ld = op->w1_per_col(); b.spec = (const C*)op->spec; b.s = w2;
-    b.s_ld = op->w2_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
+    b.s_ld = op->w2_per_col(); b.nh = op->nh; b.hs = op->hs; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
     b.plan = op->p2.plan; b.tw = tw2;
     e = stage(op, 1, cb, s, [&] {
       if (!c2) return tfk::launch_cols_fwd<T>(b, cb, op->cols_tile, s);
@@ -453,7 +456,7 @@ tf_status forward_impl(tf_op* op, int64_t B, const T* X, int64_t ldx, T* D, int6
     });
     if (e != cudaSuccess) return cuda_fail(e, "cols_fwd launch");
     tfk::RowsC2R<T> c;
-    c.src = w2; c.src_ld = op->w2_per_col(); c.nh = op->nh; c.nrows = op->sy;
+    c.src = w2; c.src_ld = op->w2_per_col(); c.nh = op->nh; c.hs = op->hs; c.nrows = op->sy;
     c.dst = D + c0 * ldd; c.dst_ld = ldd; c.out_len = op->sx; c.seq_off = op->nx - 1;
     c.scale = rs; c.plan = op->p1.plan; c.tw = tw1;
     e = stage(op, 2, cb, s, [&] {
@@ -482,7 +485,7 @@ tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int6
     tfk::RowsR2C<T> a;
     a.src = Y + c0 * ldy; a.src_ld = ldy; a.row_len = op->sx; a.nrows = op->sy;
     a.seq_off = op->nx - 1; a.scale = rs; a.dst = w2; a.dst_ld = op->w2_per_col();
-    a.nh = op->nh; a.plan = op->p1.plan; a.tw = tw1;
+    a.nh = op->nh; a.hs = op->hs; a.plan = op->p1.plan; a.tw = tw1;
     const bool c1 = op->engine == 0 && op->ct1, c2 = op->engine == 0 && op->ct2;
     cudaError_t e = stage(op, 3, cb, s, [&] {
       if (!c1) return tfk::launch_rows_r2c<T>(a, cb, op->rows_tile, s);
@@ -493,7 +496,7 @@ tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int6
     if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
     tfk::ColsAdj<T> b;
     b.z = w2; b.z_ld = op->w2_per_col(); b.spec = (const C*)op->spec; b.u = w1;
-    b.u_ld = op->w1_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
+    b.u_ld = op->w1_per_col(); b.nh = op->nh; b.hs = op->hs; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
     b.plan = op->p2.plan; b.tw = tw2;
     e = stage(op, 4, cb, s, [&] {
       if (!c2) return tfk::launch_cols_adj<T>(b, cb, op->cols_tile, s);
@@ -503,7 +506,7 @@ tf_status adjoint_impl(tf_op* op, int64_t B, const T* Y, int64_t ldy, T* X, int6
     });
     if (e != cudaSuccess) return cuda_fail(e, "cols_adj launch");
     tfk::RowsC2R<T> c;
-    c.src = w1; c.src_ld = op->w1_per_col(); c.nh = op->nh; c.nrows = op->nz * op->ny;
+    c.src = w1; c.src_ld = op->w1_per_col(); c.nh = op->nh; c.hs = op->hs; c.nrows = op->nz * op->ny;
     c.dst = X + c0 * ldx; c.dst_ld = ldx; c.out_len = op->nx; c.seq_off = 0; c.scale = cs;
     c.plan = op->p1.plan; c.tw = tw1;
     e = stage(op, 5, cb, s, [&] {
@@ -602,8 +605,10 @@ tf_status tf_get_spectra(const tf_op* op, void* dst, int64_t bytes, tf_stream st
   const int64_t need = (int64_t)op->nz * op->n2 * op->nh * (int64_t)op->csize();
   if (!dst || bytes != need)
     return fail(TF_EINVAL, "dst must hold exactly %lld bytes", (long long)need);
-  cudaError_t e = cudaMemcpyAsync(dst, op->spec, (size_t)need, cudaMemcpyDefault,
-                                  (cudaStream_t)stream);
+  // the operator keeps rows of nh values at stride hs; the copy packs them
+  cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)op->nh * op->csize(), op->spec,
+                                    (size_t)op->hs * op->csize(), (size_t)op->nh * op->csize(),
+                                    (size_t)op->nz * op->n2, cudaMemcpyDefault, (cudaStream_t)stream);
   return e == cudaSuccess ? TF_OK : cuda_fail(e, "cudaMemcpyAsync(spectra)");
 }
 
@@ -771,18 +776,18 @@ tf_status noalloc_forward(const tf_op* op, const T* x, T* d, const T* cs, const 
   const C* tw2 = (const C*)op->tw2;
   tfk::RowsR2C<T> a;
   a.src = x; a.src_ld = op->n(); a.row_len = op->nx; a.nrows = op->nz * op->ny;
-  a.seq_off = 0; a.scale = cs; a.dst = w1; a.dst_ld = op->w1_per_col(); a.nh = op->nh;
+  a.seq_off = 0; a.scale = cs; a.dst = w1; a.dst_ld = op->w1_per_col(); a.nh = op->nh; a.hs = op->hs;
   a.plan = op->p1.plan; a.tw = tw1;
   cudaError_t e = tfk::launch_rows_r2c<T>(a, 1, op->rows_tile, s);
   if (e != cudaSuccess) return cuda_fail(e, "rows_r2c launch");
   tfk::ColsFwd<T> b;
   b.z = w1; b.z_ld = op->w1_per_col(); b.spec = (const C*)op->spec; b.s = w2;
-  b.s_ld = op->w2_per_col(); b.nh = op->nh; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
+  b.s_ld = op->w2_per_col(); b.nh = op->nh; b.hs = op->hs; b.ny = op->ny; b.sy = op->sy; b.nz = op->nz;
   b.plan = op->p2.plan; b.tw = tw2;
   e = tfk::launch_cols_fwd<T>(b, 1, op->cols_tile, s);
   if (e != cudaSuccess) return cuda_fail(e, "cols_fwd launch");
   tfk::RowsC2R<T> c;
-  c.src = w2; c.src_ld = op->w2_per_col(); c.nh = op->nh; c.nrows = op->sy;
+  c.src = w2; c.src_ld = op->w2_per_col(); c.nh = op->nh; c.hs = op->hs; c.nrows = op->sy;
   c.dst = d; c.dst_ld = op->m(); c.out_len = op->sx; c.seq_off = op->nx - 1;
   c.scale = rs; c.plan = op->p1.plan; c.tw = tw1;
   e = tfk::launch_rows_c2r<T>(c, 1, op->rows_tile, s);

@@ -34,6 +34,27 @@ __host__ __device__ constexpr int twpad(int c) { return (c + 1) & ~1; }
 
 template <typename C> __device__ __forceinline__ C zero() { return mk<C>(0, 0); }
 
+// Half-spectrum rows are stored with a row stride hs that is a multiple of 16 values,
+// so the V values k1 .. k1+V-1 (k1 a multiple of V) of a row are one aligned vector.
+// Values at k1 + q >= nh lie in the row's padding: stored freely, and loaded as zero
+// with MASK (workspace rows, whose padding is never written).  The layer spectra are
+// zero in their padding, so their loads skip the mask, which would otherwise make the
+// load complete at the point of issue.
+template <int V, bool MASK, typename C>
+__device__ __forceinline__ void ld_row_vec(const C* p, int k1, int nh, bool ok, C* o) {
+  if (ok) {
+    Vec<V, C>::ld(p, o);
+    if constexpr (MASK) {
+#pragma unroll
+      for (int q = 1; q < V; ++q)
+        if (k1 + q >= nh) o[q] = zero<C>();
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) o[q] = zero<C>();
+  }
+}
+
 // Register budgets of the column kernels, as a minimum number of resident CTAs per SM
 // for __launch_bounds__ (measured with 1260-column blocks at transform lengths 64 to
 // 512: the single-precision forward kernel is fastest near 128 registers a thread, the
@@ -83,7 +104,7 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
   const ct::Buf<C, TB, V> b{buf, N * TB};
   P::template run<TB, V, NT, false>(tw, buf, b, b);
   C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
-  const int dst_ext = nrows * NH;
+  const int hs = a.hs, dst_ext = nrows * hs;
   for (int u = threadIdx.x; u < TP * NH; u += NT) {
     const int q = u / NH, k = u - q * NH;
     const int r0 = 2 * (pair0 + 2 * q);
@@ -97,10 +118,10 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
       const int ra = r0 + 2 * h, rb = ra + 1;
       if (ra >= nrows) break;
       zc[h].y = -zc[h].y;
-      if (TF_IN(kSiteR2cDst, ra * NH + k, dst_ext))
-        dst[ra * NH + k] = mk<C>(T(0.5) * (z[h].x + zc[h].x), T(0.5) * (z[h].y + zc[h].y));
-      if (rb < nrows && TF_IN(kSiteR2cDst, rb * NH + k, dst_ext))
-        dst[rb * NH + k] = mk<C>(T(0.5) * (z[h].y - zc[h].y), T(-0.5) * (z[h].x - zc[h].x));
+      if (TF_IN(kSiteR2cDst, ra * hs + k, dst_ext))
+        dst[ra * hs + k] = mk<C>(T(0.5) * (z[h].x + zc[h].x), T(0.5) * (z[h].y + zc[h].y));
+      if (rb < nrows && TF_IN(kSiteR2cDst, rb * hs + k, dst_ext))
+        dst[rb * hs + k] = mk<C>(T(0.5) * (z[h].y - zc[h].y), T(-0.5) * (z[h].x - zc[h].x));
     }
   }
 }
@@ -116,7 +137,7 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
   const int pair0 = blockIdx.x * TB;
   const int nrows = a.nrows;
   const C* src = a.src + (int64_t)blockIdx.y * a.src_ld;
-  const int src_ext = nrows * NH;
+  const int hs = a.hs, src_ext = nrows * hs;
   for (int u = threadIdx.x; u < TP * NH; u += NT) {
     const int q = u / NH, k = u - q * NH;
     const int r0 = 2 * (pair0 + 2 * q);
@@ -124,7 +145,7 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       x[i] = zero<C>();
-      if (r0 + i < nrows && TF_IN(kSiteC2rSrc, (r0 + i) * NH + k, src_ext)) x[i] = src[(r0 + i) * NH + k];
+      if (r0 + i < nrows && TF_IN(kSiteC2rSrc, (r0 + i) * hs + k, src_ext)) x[i] = src[(r0 + i) * hs + k];
     }
     const bool self = (k == 0) || (2 * k == N);
     C lo[2], hi[2];
@@ -189,34 +210,33 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>
   for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
   __syncthreads();
   const int k0 = blockIdx.x * TB;
-  const int nh = a.nh, ny = a.ny, sy = a.sy;
+  const int nh = a.nh, hs = a.hs, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
-  const int z_ext = a.nz * ny * nh, g_ext = a.nz * N * nh, s_ext = sy * nh;
+  const int z_ext = a.nz * ny * hs, g_ext = a.nz * N * hs, s_ext = sy * hs;
   const C* spec = a.spec;
   C gpre[kPre ? ITL * RL : 1][V];
   for (int r = 0; r < a.nz; ++r) {
-    const int zoff = r * ny * nh, goff = r * N * nh;
+    const int zoff = r * ny * hs, goff = r * N * hs;
 #pragma unroll
     for (int it = 0; it < ITL; ++it) {
       const int u = threadIdx.x + it * NT;
       int b0 = 0;
       const int base = LM::first_idx(u < LM::TOTAL ? u : 0, b0);
+      const int k1 = k0 + b0;
 #pragma unroll
-      for (int rr = 0; rr < RL; ++rr)
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-          const int k1 = k0 + b0 + q;
-          const int e = goff + (base + rr * NSL) * nh + k1;
-          gpre[it * RL + rr][q] = zero<C>();
-          if (u < LM::TOTAL && k1 < nh && TF_IN(kSiteFwdSpec, e, g_ext)) gpre[it * RL + rr][q] = spec[e];
-        }
+      for (int rr = 0; rr < RL; ++rr) {
+        const int e = goff + (base + rr * NSL) * hs + k1;
+        ld_row_vec<V, false>(spec + e, k1, nh, u < LM::TOTAL && k1 < nh && TF_IN(kSiteFwdSpec, e + V - 1, g_ext),
+                             gpre[it * RL + rr]);
+      }
     }
     const bool first_layer = (r == 0);
+    // (one load per value: a vector load here measured slower, unlike in cols_adj)
     auto load = [=](int idx, int b0, C* o) {
 #pragma unroll
       for (int q = 0; q < V; ++q) {
         const int k1 = k0 + b0 + q;
-        const int e = zoff + idx * nh + k1;
+        const int e = zoff + idx * hs + k1;
         o[q] = zero<C>();
         if (idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e, z_ext)) o[q] = z[e];
       }
@@ -225,17 +245,15 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>
       C cur[V];
       const bool acc_ok = TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB);
       if (!first_layer && acc_ok) Vec<V, C>::ld(acc + idx * TB + b0, cur);
+      C gv[V];
+      if constexpr (!kPre) {
+        const int k1 = k0 + b0;
+        const int e = goff + idx * hs + k1;
+        ld_row_vec<V, false>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteFwdSpec, e + V - 1, g_ext), gv);
+      }
 #pragma unroll
       for (int q = 0; q < V; ++q) {
-        C g;
-        if constexpr (kPre) {
-          g = gpre[slot][q];
-        } else {
-          const int k1 = k0 + b0 + q;
-          const int e = goff + idx * nh + k1;
-          g = zero<C>();
-          if (k1 < nh && TF_IN(kSiteFwdSpec, e, g_ext)) g = spec[e];
-        }
+        const C g = kPre ? gpre[slot][q] : gv[q];
         const C p = cmul(g, v[q]);
         cur[q] = first_layer ? p : cadd(cur[q], p);
       }
@@ -248,13 +266,9 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>
     if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::ld(acc + idx * TB + b0, o);
   };
   auto store = [=](int idx, int b0, const C* v, int) {
-    const int j = idx - (ny - 1);
-    if (j < 0 || j >= sy) return;
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const int k1 = k0 + b0 + q;
-      if (k1 < nh && TF_IN(kSiteFwdS, j * nh + k1, s_ext)) s[j * nh + k1] = v[q];
-    }
+    const int j = idx - (ny - 1), k1 = k0 + b0;
+    if (j < 0 || j >= sy || k1 >= nh) return;
+    if (TF_IN(kSiteFwdS, j * hs + k1 + V - 1, s_ext)) Vec<V, C>::st(s + j * hs + k1, v);
   };
   P::template run<TB, V, NT, true>(tw, buf, lacc, store);
 }
@@ -272,17 +286,13 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kAdjThreadsPerSM<T>
   for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
   __syncthreads();
   const int k0 = blockIdx.x * TB;
-  const int nh = a.nh, ny = a.ny, sy = a.sy;
+  const int nh = a.nh, hs = a.hs, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
-  const int z_ext = sy * nh, g_ext = a.nz * N * nh, u_ext = a.nz * ny * nh;
+  const int z_ext = sy * hs, g_ext = a.nz * N * hs, u_ext = a.nz * ny * hs;
   auto load = [=](int idx, int b0, C* o) {
-    const int j = idx - (ny - 1);
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const int k1 = k0 + b0 + q;
-      o[q] = zero<C>();
-      if (j >= 0 && j < sy && k1 < nh && TF_IN(kSiteAdjZ, j * nh + k1, z_ext)) o[q] = z[j * nh + k1];
-    }
+    const int j = idx - (ny - 1), k1 = k0 + b0;
+    ld_row_vec<V, true>(z + j * hs + k1, k1, nh,
+                  j >= 0 && j < sy && k1 < nh && TF_IN(kSiteAdjZ, j * hs + k1 + V - 1, z_ext), o);
   };
   auto sacc = [=](int idx, int b0, const C* v, int) {
     if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::st(acc + idx * TB + b0, v);
@@ -291,26 +301,21 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kAdjThreadsPerSM<T>
   C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
   const C* spec = a.spec;
   for (int r = 0; r < a.nz; ++r) {
-    const int goff = r * N * nh, uoff = r * ny * nh;
+    const int goff = r * N * hs, uoff = r * ny * hs;
     auto prod = [=](int idx, int b0, C* o) {
-      C cur[V];
+      C cur[V], gv[V];
       if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::ld(acc + idx * TB + b0, cur);
+      const int k1 = k0 + b0;
+      const int e = goff + idx * hs + k1;
+      ld_row_vec<V, false>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteAdjSpec, e + V - 1, g_ext), gv);
 #pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const int k1 = k0 + b0 + q;
-        const int e = goff + idx * nh + k1;
-        o[q] = zero<C>();
-        if (k1 < nh && TF_IN(kSiteAdjSpec, e, g_ext)) o[q] = cmulc(cur[q], spec[e]);
-      }
+      for (int q = 0; q < V; ++q) o[q] = cmulc(cur[q], gv[q]);
     };
     auto store = [=](int idx, int b0, const C* v, int) {
-      if (idx >= ny) return;
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const int k1 = k0 + b0 + q;
-        const int e = uoff + idx * nh + k1;
-        if (k1 < nh && TF_IN(kSiteAdjU, e, u_ext)) u[e] = v[q];
-      }
+      const int k1 = k0 + b0;
+      if (idx >= ny || k1 >= nh) return;
+      const int e = uoff + idx * hs + k1;
+      if (TF_IN(kSiteAdjU, e + V - 1, u_ext)) Vec<V, C>::st(u + e, v);
     };
     P::template run<TB, V, NT, true>(tw, buf, prod, store);
   }

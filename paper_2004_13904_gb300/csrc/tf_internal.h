@@ -12,39 +12,40 @@ namespace tfk {
 // Row rho of column b holds row_len reals at src + b*src_ld + rho*row_len; they are
 // scaled by scale[rho*row_len + n] (if non-null), placed at [seq_off, seq_off+row_len)
 // of a zero sequence of length plan.n, transformed, and the nh = n/2+1 outputs are
-// written to dst + b*dst_ld + rho*nh.  Two rows share one complex transform.
+// written to dst + b*dst_ld + rho*hs (hs >= nh: the row stride of half-spectrum
+// buffers).  Two rows share one complex transform.
 template <typename T> struct RowsR2C {
   const T* src; int64_t src_ld; int row_len; int nrows; int seq_off; const T* scale;
-  typename CT<T>::C* dst; int64_t dst_ld; int nh;
+  typename CT<T>::C* dst; int64_t dst_ld; int nh; int hs;
   FftPlan plan; const typename CT<T>::C* tw;
 };
 
 // Rows stage, half spectrum -> real window: inverse of the above; outputs sequence
 // entries [seq_off, seq_off+out_len) times scale[rho*out_len + i] to dst.
 template <typename T> struct RowsC2R {
-  const typename CT<T>::C* src; int64_t src_ld; int nh; int nrows;
+  const typename CT<T>::C* src; int64_t src_ld; int nh; int hs; int nrows;
   T* dst; int64_t dst_ld; int out_len; int seq_off; const T* scale;
   FftPlan plan; const typename CT<T>::C* tw;
 };
 
 // Column stage of G x: for each k1 column, FFT along y of every layer's rows,
 // multiply-accumulate with the layer spectra (sum over layers in the frequency domain),
-// inverse FFT, keep rows [ny-1, ny-1+sy).
+// inverse FFT, keep rows [ny-1, ny-1+sy).  Rows of nh values with row stride hs.
 template <typename T> struct ColsFwd {
-  const typename CT<T>::C* z; int64_t z_ld;       // [nz*ny][nh] per column
-  const typename CT<T>::C* spec;                  // [nz][n2][nh]
-  typename CT<T>::C* s; int64_t s_ld;             // [sy][nh] per column
-  int nh, ny, sy, nz;
+  const typename CT<T>::C* z; int64_t z_ld;       // [nz*ny][hs] per column
+  const typename CT<T>::C* spec;                  // [nz][n2][hs]
+  typename CT<T>::C* s; int64_t s_ld;             // [sy][hs] per column
+  int nh, hs, ny, sy, nz;
   FftPlan plan; const typename CT<T>::C* tw;
 };
 
 // Column stage of G^T y: FFT along y of the data rows placed at [ny-1, ny-1+sy), then
 // per layer multiply by the conjugate spectrum, inverse FFT, keep rows [0, ny).
 template <typename T> struct ColsAdj {
-  const typename CT<T>::C* z; int64_t z_ld;       // [sy][nh] per column
-  const typename CT<T>::C* spec;                  // [nz][n2][nh]
-  typename CT<T>::C* u; int64_t u_ld;             // [nz*ny][nh] per column
-  int nh, ny, sy, nz;
+  const typename CT<T>::C* z; int64_t z_ld;       // [sy][hs] per column
+  const typename CT<T>::C* spec;                  // [nz][n2][hs]
+  typename CT<T>::C* u; int64_t u_ld;             // [nz*ny][hs] per column
+  int nh, hs, ny, sy, nz;
   FftPlan plan; const typename CT<T>::C* tw;
 };
 
@@ -60,8 +61,8 @@ struct TableArgs {
 };
 
 struct SpecArgs {
-  const double2* ht; int n2min; int nh; int nz; double scale;
-  double2* spec;           // [nz][n2][nh]
+  const double2* ht; int n2min; int nh; int nz; double scale;   // ht: [nz][n2min][nh]
+  double2* spec; int hs;   // [nz][n2][hs]
   FftPlan plan; const double2* tw;
 };
 

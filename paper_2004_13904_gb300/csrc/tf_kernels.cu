@@ -76,11 +76,11 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(const RowsR2C<T> a) {
     const C z = fin[k * ld + pp];
     C zc = fin[(k ? N - k : 0) * ld + pp];
     zc.y = -zc.y;
-    const int64_t ext = (int64_t)a.nrows * nh;
-    if (TF_IN(100 + kSiteR2cDst, (int64_t)ra * nh + k, ext))
-      dst[(int64_t)ra * nh + k] = mk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
-    if (rb < a.nrows && TF_IN(100 + kSiteR2cDst, (int64_t)rb * nh + k, ext))
-      dst[(int64_t)rb * nh + k] = mk<C>(T(0.5) * (z.y - zc.y), T(-0.5) * (z.x - zc.x));
+    const int64_t ext = (int64_t)a.nrows * a.hs;
+    if (TF_IN(100 + kSiteR2cDst, (int64_t)ra * a.hs + k, ext))
+      dst[(int64_t)ra * a.hs + k] = mk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
+    if (rb < a.nrows && TF_IN(100 + kSiteR2cDst, (int64_t)rb * a.hs + k, ext))
+      dst[(int64_t)rb * a.hs + k] = mk<C>(T(0.5) * (z.y - zc.y), T(-0.5) * (z.x - zc.x));
   }
 }
 
@@ -102,10 +102,10 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r(const RowsC2R<T> a) {
   for (int u = threadIdx.x; u < TB * nh; u += blockDim.x) {
     const int pp = u / nh, k = u - pp * nh;
     const int ra = 2 * (pair0 + pp), rb = ra + 1;
-    const int64_t ext = (int64_t)a.nrows * nh;
+    const int64_t ext = (int64_t)a.nrows * a.hs;
     C xa = czero<C>(), xb = czero<C>();
-    if (ra < a.nrows && TF_IN(100 + kSiteC2rSrc, (int64_t)ra * nh + k, ext)) xa = src[(int64_t)ra * nh + k];
-    if (rb < a.nrows && TF_IN(100 + kSiteC2rSrc, (int64_t)rb * nh + k, ext)) xb = src[(int64_t)rb * nh + k];
+    if (ra < a.nrows && TF_IN(100 + kSiteC2rSrc, (int64_t)ra * a.hs + k, ext)) xa = src[(int64_t)ra * a.hs + k];
+    if (rb < a.nrows && TF_IN(100 + kSiteC2rSrc, (int64_t)rb * a.hs + k, ext)) xb = src[(int64_t)rb * a.hs + k];
     const bool self = (k == 0) || (2 * k == N);
     if (self) { xa.y = T(0); xb.y = T(0); }
     bufB[k * ld + pp] = mk<C>(xa.x - xb.y, xa.y + xb.x);
@@ -147,23 +147,23 @@ __global__ void __launch_bounds__(kThreads) k_cols_fwd(const ColsFwd<T> a) {
   __syncthreads();
 
   const int k0 = blockIdx.x * TK;
-  const int nh = a.nh, ny = a.ny, sy = a.sy;
+  const int nh = a.nh, hs = a.hs, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
-  const int64_t z_ext = (int64_t)a.nz * ny * nh, g_ext = (int64_t)a.nz * N * nh;
+  const int64_t z_ext = (int64_t)a.nz * ny * hs, g_ext = (int64_t)a.nz * N * hs;
   const C* spec = a.spec;
   for (int r = 0; r < a.nz; ++r) {
-    const int64_t zoff = (int64_t)r * ny * nh, goff = (int64_t)r * N * nh;
+    const int64_t zoff = (int64_t)r * ny * hs, goff = (int64_t)r * N * hs;
     const bool first_layer = (r == 0);
     auto load = [=](int idx, int tk) -> C {
       const int k1 = k0 + tk;
-      const int64_t e = zoff + (int64_t)idx * nh + k1;
+      const int64_t e = zoff + (int64_t)idx * hs + k1;
       C v = czero<C>();
       if (idx < ny && k1 < nh && TF_IN(100 + kSiteFwdZ, e, z_ext)) v = z[e];
       return v;
     };
     auto mac = [=](int idx, int tk, C v) {
       const int k1 = k0 + tk;
-      const int64_t e = goff + (int64_t)idx * nh + k1;
+      const int64_t e = goff + (int64_t)idx * hs + k1;
       C g = czero<C>();
       if (k1 < nh && TF_IN(100 + kSiteFwdSpec, e, g_ext)) g = spec[e];
       const C p = cmul(g, v);
@@ -173,11 +173,11 @@ __global__ void __launch_bounds__(kThreads) k_cols_fwd(const ColsFwd<T> a) {
     fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, mac);
   }
   C* s = a.s + (int64_t)blockIdx.y * a.s_ld;
-  const int64_t s_ext = (int64_t)sy * nh;
+  const int64_t s_ext = (int64_t)sy * hs;
   auto store = [=](int idx, int tk, C v) {
     const int j = idx - (ny - 1), k1 = k0 + tk;
-    if (j >= 0 && j < sy && k1 < nh && TF_IN(100 + kSiteFwdS, (int64_t)j * nh + k1, s_ext))
-      s[(int64_t)j * nh + k1] = v;
+    if (j >= 0 && j < sy && k1 < nh && TF_IN(100 + kSiteFwdS, (int64_t)j * hs + k1, s_ext))
+      s[(int64_t)j * hs + k1] = v;
   };
   fft_run<true>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, SmemLoad<C>{acc, TK, N * TK}, store);
 }
@@ -195,32 +195,32 @@ __global__ void __launch_bounds__(kThreads) k_cols_adj(const ColsAdj<T> a) {
   __syncthreads();
 
   const int k0 = blockIdx.x * TK;
-  const int nh = a.nh, ny = a.ny, sy = a.sy;
+  const int nh = a.nh, hs = a.hs, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
-  const int64_t z_ext = (int64_t)sy * nh, g_ext = (int64_t)a.nz * N * nh;
-  const int64_t u_ext = (int64_t)a.nz * ny * nh;
+  const int64_t z_ext = (int64_t)sy * hs, g_ext = (int64_t)a.nz * N * hs;
+  const int64_t u_ext = (int64_t)a.nz * ny * hs;
   const C* spec = a.spec;
   auto load = [=](int idx, int tk) -> C {
     const int j = idx - (ny - 1), k1 = k0 + tk;
     C v = czero<C>();
-    if (j >= 0 && j < sy && k1 < nh && TF_IN(100 + kSiteAdjZ, (int64_t)j * nh + k1, z_ext))
-      v = z[(int64_t)j * nh + k1];
+    if (j >= 0 && j < sy && k1 < nh && TF_IN(100 + kSiteAdjZ, (int64_t)j * hs + k1, z_ext))
+      v = z[(int64_t)j * hs + k1];
     return v;
   };
   fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, SmemStore<C>{acc, TK, N * TK});
   C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
   for (int r = 0; r < a.nz; ++r) {
-    const int64_t goff = (int64_t)r * N * nh, uoff = (int64_t)r * ny * nh;
+    const int64_t goff = (int64_t)r * N * hs, uoff = (int64_t)r * ny * hs;
     auto prod = [=](int idx, int tk) -> C {
       const int k1 = k0 + tk;
-      const int64_t e = goff + (int64_t)idx * nh + k1;
+      const int64_t e = goff + (int64_t)idx * hs + k1;
       C v = czero<C>();
       if (k1 < nh && TF_IN(100 + kSiteAdjSpec, e, g_ext)) v = cmulc(acc[idx * TK + tk], spec[e]);
       return v;
     };
     auto store = [=](int idx, int tk, C v) {
       const int k1 = k0 + tk;
-      const int64_t e = uoff + (int64_t)idx * nh + k1;
+      const int64_t e = uoff + (int64_t)idx * hs + k1;
       if (idx < ny && k1 < nh && TF_IN(100 + kSiteAdjU, e, u_ext)) u[e] = v;
     };
     fft_run<true>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, prod, store);
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(const SpecArgs a) {
   __syncthreads();
   const int k0 = blockIdx.x * TK, r = blockIdx.y, nh = a.nh, n2min = a.n2min;
   const C* ht = a.ht + (int64_t)r * n2min * nh;
-  C* out = a.spec + (int64_t)r * N * nh;
+  C* out = a.spec + (int64_t)r * N * a.hs;
   const double sc = a.scale;
   auto load = [=](int idx, int tk) -> C {
     const int k1 = k0 + tk;
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(const SpecArgs a) {
   };
   auto store = [=](int idx, int tk, C v) {
     const int k1 = k0 + tk;
-    if (k1 < nh) out[(int64_t)idx * nh + k1] = cscale(v, sc);
+    if (k1 < nh) out[(int64_t)idx * a.hs + k1] = cscale(v, sc);
   };
   fft_run<false>(a.plan, tw, bufA, bufB, TK, Log2<TK>::value, load, store);
 }
