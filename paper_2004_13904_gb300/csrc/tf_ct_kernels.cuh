@@ -69,7 +69,9 @@ template <typename T> constexpr int kAdjThreadsPerSM = 640;
 // The row kernels stage and unpack two adjacent sequences (2q, 2q + 1) per thread and
 // element: one 16-byte shared-memory access (the pair is adjacent in the swizzled
 // buffer), and the four real rows 2 (pair0 + 2q) + 0..3 that feed them.
-template <typename T, class P, int TB, int V, int NT>
+// ZHI: the rows' data lies in [0, N/2) of the sequence, so staging fills only that half
+// and the first pass takes the upper half as zero.
+template <typename T, class P, int TB, int V, int NT, bool ZHI>
 __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2;
@@ -82,8 +84,9 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
   const int len = a.row_len, off = a.seq_off, nrows = a.nrows;
   const int src_ext = nrows * len;
   const T* scale = a.scale;
-  for (int u = threadIdx.x; u < TP * N; u += NT) {
-    const int q = u / N, n = u - q * N;
+  constexpr int NS = ZHI && P::can_zero_hi ? N / 2 : N;   // staged rows of the buffer
+  for (int u = threadIdx.x; u < TP * NS; u += NT) {
+    const int q = u / NS, n = u - q * NS;
     const int r0 = 2 * (pair0 + 2 * q);
     const int e = n - off;
     T x[4] = {T(0), T(0), T(0), T(0)};
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
   }
   __syncthreads();
   const ct::Buf<C, TB, V> b{buf, N * TB};
-  P::template run<TB, V, NT, false>(tw, buf, b, b);
+  P::template run<TB, V, NT, false, ZHI>(tw, buf, b, b);
   C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int hs = a.hs, dst_ext = nrows * hs;
   for (int u = threadIdx.x; u < TP * NH; u += NT) {
@@ -192,10 +195,11 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
 // double kernels measured no gain from it).
 template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::value;
 
-// Column stage of G x.  In single precision each thread loads the spectrum values that
+// Column stage of G x (ZHI: ny <= N/2, the layer rows fill the lower half).  In single
+// precision each thread loads the spectrum values that
 // its last forward pass multiplies at the start of every layer, into registers, so that
 // their global-memory latency overlaps the layer's first passes.
-template <typename T, class P, int TB, int V, int NT>
+template <typename T, class P, int TB, int V, int NT, bool ZHI>
 __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>)) k_cols_fwd(const ColsFwd<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n;
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>
       }
       if (acc_ok) Vec<V, C>::st(acc + idx * TB + b0, cur);
     };
-    P::template run<TB, V, NT, false>(tw, buf, load, mac);
+    P::template run<TB, V, NT, false, ZHI>(tw, buf, load, mac);
   }
   C* s = a.s + (int64_t)blockIdx.y * a.s_ld;
   auto lacc = [=](int idx, int b0, C* o) {
@@ -348,15 +352,22 @@ template <int N> struct Tiles<double, N> {
   static constexpr int TB = N <= 96 ? 8 : 4, V = 2, NT = 64;
 };
 
+template <auto K, class A>
+cudaError_t launch_k(const A& a, dim3 grid, int nt, size_t sm, cudaStream_t s) {
+  cudaError_t e = set_smem<K>(sm);
+  if (e != cudaSuccess) return e;
+  K<<<grid, nt, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, class P>
 cudaError_t rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
-  constexpr auto k = k_rows_r2c<T, P, TL::TB, TL::V, TL::NT>;
   const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB) * sizeof(typename CT<T>::C);
-  cudaError_t e = set_smem<k>(sm);
-  if (e != cudaSuccess) return e;
-  k<<<dim3(cdiv((a.nrows + 1) / 2, TL::TB), ncols), TL::NT, sm, s>>>(a);
-  return cudaGetLastError();
+  const dim3 grid(cdiv((a.nrows + 1) / 2, TL::TB), ncols);
+  if (P::can_zero_hi && a.seq_off >= 0 && a.seq_off + a.row_len <= P::n / 2)
+    return launch_k<k_rows_r2c<T, P, TL::TB, TL::V, TL::NT, true>>(a, grid, TL::NT, sm, s);
+  return launch_k<k_rows_r2c<T, P, TL::TB, TL::V, TL::NT, false>>(a, grid, TL::NT, sm, s);
 }
 template <typename T, class P>
 cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
@@ -371,12 +382,11 @@ cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
 template <typename T, class P>
 cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
-  constexpr auto k = k_cols_fwd<T, P, TL::TB, TL::V, TL::NT>;
   const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
-  cudaError_t e = set_smem<k>(sm);
-  if (e != cudaSuccess) return e;
-  k<<<dim3(cdiv(a.nh, TL::TB), ncols), TL::NT, sm, s>>>(a);
-  return cudaGetLastError();
+  const dim3 grid(cdiv(a.nh, TL::TB), ncols);
+  if (P::can_zero_hi && a.ny <= P::n / 2)
+    return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, true>>(a, grid, TL::NT, sm, s);
+  return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, false>>(a, grid, TL::NT, sm, s);
 }
 template <typename T, class P>
 cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {

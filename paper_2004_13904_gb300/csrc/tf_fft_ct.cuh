@@ -101,8 +101,36 @@ template <int R, int Ns, int N, int TB, int V> struct PassMap {
 // One radix-R pass with stride Ns over TB sequences, V per thread, NT threads.
 // Loader: ld(idx, b0, C out[V]); storer: st(idx, b0, const C in[V], slot) where slot =
 // it * R + r numbers the thread's outputs of the pass (a compile-time constant).
-template <int R, int Ns, int N, int TB, int V, int NT, bool INV, typename C, class L, class S>
+// Radix-R butterfly whose inputs r >= R/2 are zero (first pass of a zero-upper-half
+// sequence): the same outputs as Dft<R> without the additions of those zeros.
+template <int R, bool INV, typename C> struct DftZhi {
+  static __device__ __forceinline__ void run(C* v) { Dft<R, INV, C>::run(v); }
+};
+template <bool INV, typename C> struct DftZhi<8, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    typedef decltype(C::x) T;
+    // length-4 transforms of (v0, v2, 0, 0) and (v1, v3, 0, 0)
+    const C m2 = mul_mi<INV>(v[2]), m3 = mul_mi<INV>(v[3]);
+    const C e[4] = {cadd(v[0], v[2]), cadd(v[0], m2), csub(v[0], v[2]), csub(v[0], m2)};
+    const C o[4] = {cadd(v[1], v[3]), cadd(v[1], m3), csub(v[1], v[3]), csub(v[1], m3)};
+    const T h = T(0.7071067811865475244008444);
+    const C o1 = INV ? mk<C>(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                     : mk<C>(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+    const C o2 = mul_mi<INV>(o[2]);
+    const C o3 = INV ? mk<C>(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                     : mk<C>(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+  }
+};
+
+// ZHI (first pass only, R even): the inputs of the upper half, rows >= N/2 (the r >= R/2
+// inputs of every task), are known zeros; they are neither loaded nor computed with.
+template <int R, int Ns, int N, int TB, int V, int NT, bool INV, bool ZHI = false, typename C, class L, class S>
 __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, const S& st) {
+  static_assert(!ZHI || (Ns == 1 && R % 2 == 0), "zero upper half needs an even first radix");
   constexpr int NB = N / R;
   constexpr int G = TB / V;
   constexpr int TOTAL = NB * G;
@@ -117,7 +145,12 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         C t[V];
-        ld(j + r * NB, b0, t);
+        if (ZHI && r >= R / 2) {
+#pragma unroll
+          for (int q = 0; q < V; ++q) t[q] = mk<C>(0, 0);
+        } else {
+          ld(j + r * NB, b0, t);
+        }
 #pragma unroll
         for (int q = 0; q < V; ++q) v[it][q][r] = t[q];
       }
@@ -134,7 +167,10 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
         }
       }
 #pragma unroll
-      for (int q = 0; q < V; ++q) Dft<R, INV, C>::run(v[it][q]);
+      for (int q = 0; q < V; ++q) {
+        if constexpr (ZHI) DftZhi<R, INV, C>::run(v[it][q]);
+        else Dft<R, INV, C>::run(v[it][q]);
+      }
     }
   }
   if (kInPlace) __syncthreads();
@@ -160,16 +196,16 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
 // `last`, the others use the shared buffer.  Twiddle layout as in FftPlan.
 template <int N, int Ns, int TwOff, int... Rs> struct Run;
 template <int N, int Ns, int TwOff, int R, int... Rest> struct Run<N, Ns, TwOff, R, Rest...> {
-  template <int TB, int V, int NT, bool INV, bool FIRST, typename C, class L0, class SL>
+  template <int TB, int V, int NT, bool INV, bool FIRST, bool ZHI, typename C, class L0, class SL>
   static __device__ __forceinline__ void go(const C* tw, C* buf, const L0& first, const SL& last) {
     constexpr bool LAST = sizeof...(Rest) == 0;
     const Buf<C, TB, V> b{buf, N * TB};
-    if constexpr (FIRST && LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, first, last);
-    else if constexpr (FIRST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, first, b);
+    if constexpr (FIRST && LAST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, last);
+    else if constexpr (FIRST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, b);
     else if constexpr (LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, last);
     else pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, b);
     if constexpr (!LAST)
-      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false>(
+      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false, false>(
           tw, buf, first, last);
   }
 };
@@ -181,13 +217,18 @@ template <int R, int... Rest> struct LastOf<R, Rest...> {
   static constexpr int prod_before = R * LastOf<Rest...>::prod_before;
 };
 
+template <int R, int... Rest> struct FirstOf { static constexpr int r = R; };
+
 template <int N, int... Rs> struct Plan {
   static constexpr int n = N;
   static constexpr int last_r = LastOf<Rs...>::r;          // radix of the last pass
   static constexpr int last_ns = LastOf<Rs...>::prod_before;  // its stride
-  template <int TB, int V, int NT, bool INV, typename C, class L0, class SL>
+  // The upper half of the input may be declared zero (run<..., ZHI = true>) when the
+  // first radix is even.
+  static constexpr bool can_zero_hi = FirstOf<Rs...>::r % 2 == 0;
+  template <int TB, int V, int NT, bool INV, bool ZHI = false, typename C, class L0, class SL>
   static __device__ __forceinline__ void run(const C* tw, C* buf, const L0& first, const SL& last) {
-    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true>(tw, buf, first, last);
+    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi>(tw, buf, first, last);
   }
 };
 
