@@ -206,6 +206,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-chunks", type=int, default=8,
+                    help="column chunks of the host-buffer pipeline (Operator.products_host)")
     ap.add_argument("--columns", type=int, default=BLOCK,
                     help="columns per block (default: the 1260-column RSVD block); smaller "
                          "blocks serve profiling captures")
@@ -277,14 +279,12 @@ def main():
         Yh = Y.cpu().pin_memory()
         Dh = torch.empty((cols_per_rank, g.m), dtype=dt, pin_memory=True)
         XTh = torch.empty((cols_per_rank, g.n), dtype=dt, pin_memory=True)
-        op.matmat_host(Xh, Dh)
-        op.rmatmat_host(Yh, XTh)
+        op.products_host(Xh, Yh, Dh, XTh, chunks=args.e2e_chunks)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            op.matmat_host(Xh, Dh)
-            op.rmatmat_host(Yh, XTh)
+            op.products_host(Xh, Yh, Dh, XTh, chunks=args.e2e_chunks)
             torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         barrier()

@@ -185,13 +185,7 @@ class Operator:
         if not hasattr(self, "_copy_streams"):
             self._copy_streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
         s_in, s_out = self._copy_streams
-        key = (H.shape[1], rows_out, B)
-        bufs = getattr(self, "_host_bufs", None)
-        if bufs is None or bufs[0] != key:
-            din = torch.empty((B, H.shape[1]), dtype=self.dtype, device=self.device)
-            dout = torch.empty((B, rows_out), dtype=self.dtype, device=self.device)
-            self._host_bufs = bufs = (key, din, dout)
-        _, din, dout = bufs
+        din, dout = self._device_bufs(B, H.shape[1], rows_out)
         n = max(1, min(chunks, B))
         edges = [B * i // n for i in range(n + 1)]
         s_in.wait_stream(main)
@@ -209,6 +203,58 @@ class Operator:
                 out_host[a:b].copy_(dout[a:b], non_blocking=True)
         main.wait_stream(s_out)
         return out_host
+
+    def _device_bufs(self, B, rows_in, rows_out):
+        """Device staging blocks for host-buffer products, kept per shape."""
+        torch = _torch()
+        cache = self.__dict__.setdefault("_host_bufs", {})
+        key = (B, rows_in, rows_out)
+        if key not in cache:
+            cache[key] = (torch.empty((B, rows_in), dtype=self.dtype, device=self.device),
+                          torch.empty((B, rows_out), dtype=self.dtype, device=self.device))
+        return cache[key]
+
+    def products_host(self, X_host, Y_host, D_host=None, XT_host=None, chunks: int = 4):
+        """G X and G^T Y for two independent pinned host blocks X (B1 x n) and Y (B2 x m),
+        into pinned host blocks D (B1 x m) and XT (B2 x n); returns (D, XT).
+
+        Both products run as one pipeline of `chunks` column chunks: per chunk, Y's copy
+        in, the G^T product and the copy out of its result, then the same for X and G.  The
+        large copies of the two directions (X in, G^T Y out) then overlap on the
+        full-duplex host link instead of following each other.  The caller's current
+        stream is ordered after all of it."""
+        torch = _torch()
+        B1, B2 = X_host.shape[0], Y_host.shape[0]
+        if D_host is None:
+            D_host = torch.empty((B1, self.m), dtype=self.dtype, pin_memory=True)
+        if XT_host is None:
+            XT_host = torch.empty((B2, self.n), dtype=self.dtype, pin_memory=True)
+        main = torch.cuda.current_stream(self.device)
+        if not hasattr(self, "_copy_streams"):
+            self._copy_streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
+        s_in, s_out = self._copy_streams
+        xin, dout = self._device_bufs(B1, self.n, self.m)
+        yin, xtout = self._device_bufs(B2, self.m, self.n)
+        n = max(1, chunks)
+        ex = [B1 * i // n for i in range(n + 1)]
+        ey = [B2 * i // n for i in range(n + 1)]
+        s_in.wait_stream(main)
+        s_out.wait_stream(main)
+        for c in range(n):
+            for (H, din, dres, R, e, fn) in ((Y_host, yin, xtout, XT_host, ey, self.rmatmat),
+                                             (X_host, xin, dout, D_host, ex, self.matmat)):
+                a, b = e[c], e[c + 1]
+                if a == b:
+                    continue
+                with torch.cuda.stream(s_in):
+                    din[a:b].copy_(H[a:b], non_blocking=True)
+                main.wait_stream(s_in)
+                fn(din[a:b], out=dres[a:b])
+                s_out.wait_stream(main)
+                with torch.cuda.stream(s_out):
+                    R[a:b].copy_(dres[a:b], non_blocking=True)
+        main.wait_stream(s_out)
+        return D_host, XT_host
 
     def matmat_host(self, X_host, out_host=None, chunks: int = 4):
         """G X for a pinned host block X (B x n) into pinned host memory (B x m)."""

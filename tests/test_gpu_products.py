@@ -240,3 +240,20 @@ def test_host_pipeline_matches_device_products(chunks):
     torch.cuda.synchronize()
     assert torch.equal(D, op.matmat(X.cuda()).cpu())
     assert torch.equal(XT, op.rmatmat(Y.cuda()).cpu())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("chunks", [1, 3, 20])
+def test_products_host_matches_device_products(chunks):
+    # both directions in one pipeline, blocks of different widths (and chunks > columns)
+    torch = _torch()
+    g = SMALL[7][1]
+    op = make_op(g, "gravity", 90.0, 0.0, "f32")
+    rng = np.random.default_rng(13)
+    X = torch.tensor(rng.standard_normal((9, g.n)), dtype=torch.float32).pin_memory()
+    Y = torch.tensor(rng.standard_normal((5, g.m)), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        D, XT = op.products_host(X, Y, chunks=chunks)
+        torch.cuda.synchronize()
+        assert torch.equal(D, op.matmat(X.cuda()).cpu())
+        assert torch.equal(XT, op.rmatmat(Y.cuda()).cpu())
