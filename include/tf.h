@@ -200,6 +200,81 @@ tf_status tf_rows_axpy(tf_dtype dtype, const void* A, int64_t lda, int64_t k, in
  * Synchronises the stream.  Errors: TF_EINVAL, TF_ENOMEM, TF_ECUDA. */
 tf_status tf_peak_probe(tf_dtype dtype, double* tflops, tf_stream stream);
 
+/* ---- IRLS focusing inversion drivers (Sec. 2.3, Alg. 1, Alg. 2, Sec. 3.1) -------------
+ *
+ * Both drivers minimise the focusing functional of Eq. (4) by iteratively reweighted
+ * least squares on the operator's products:
+ *   W = W_z W_L^(k), W_z = diag(zbar_r^(-beta)) per layer (zbar_r the mean depth of layer
+ *   r below the stations), W_L^(1) = I, (W_L^(k))_ii = ((m_i^(k-1) - m_i^(k-2))^2 +
+ *   eps2)^((lam - 2)/4);  G~ = W_d G W^-1 with W_d = diag(1/sigma)  (Eq. (10));
+ *   r~ = W_d (d_obs - G m^(k-1));  the projected problem gives z with
+ *   min ||G~ z - r~||^2 + alpha^2 ||z||^2;  m^(k) = clip(m^(k-1) + W^-1 z, lower, upper);
+ *   alpha^(1) from Eq. (11) (mean over the t retained singular values above 1e-14 s_1),
+ *   alpha^(k>1) minimises UPRE for whitened noise on the t retained terms (a 200-point
+ *   log grid on [max(s_t, 1e-14 s_1)/10, s_1], then 80 golden-section steps in log alpha
+ *   between the best point's neighbours);  stop after kmax iterations or, with chi2_stop,
+ *   once ||W_d (G m^(k) - d_obs)||^2 <= m + sqrt(2 m)  (Eq. (12)).
+ * tf_gkb projects with t_p steps of Golub-Kahan bidiagonalisation of G~ started from r~
+ * (Alg. 1) with re-orthogonalisation of both bases (classical Gram-Schmidt applied
+ * twice, or modified Gram-Schmidt), UPRE on the t largest singular values of the
+ * (t_p+1) x t_p bidiagonal B, and the Tikhonov solution on all t_p terms, i.e. the least
+ * squares solution of [B; alpha I] y = [||r~|| e_1; 0] (Givens QR), z = A y.
+ * tf_rsvd projects with the randomised SVD of Alg. 2 with one power iteration from the
+ * caller's Gaussian test matrix Omega, keeps the t largest singular values of B = G~ Q
+ * (eigen-decomposition of B^T B) and z = Q V_t Gamma(alpha) U_t^T r~.
+ *
+ * Arguments: d_obs, sigma (length m) and m_out (length n) are DEVICE arrays of the
+ * operator's dtype; omega (tf_rsvd) is a DEVICE t_p x m array, row-major (row j = the j-th
+ * test vector).  m_out receives m^(K), the last iterate (m^(0) = 0).  The drivers
+ * allocate their own device workspace (A: t_p x n and H: (t_p+1) x m for tf_gkb; five
+ * t_p x max(n, m) blocks for tf_rsvd), run on `stream`, and synchronise it before
+ * returning.  The projected problems are solved on the host in FP64.  tf_rsvd uses
+ * cuSOLVER (QR, symmetric eigen-decomposition) and cuBLAS (B^T B).  Errors: TF_EINVAL
+ * (bad sizes or parameters, t > t_p, tf_rsvd with t_p > min(m, n)), TF_ENOMEM, TF_ECUDA,
+ * TF_ENOTCONV (the host eigenvalue iteration did not converge). */
+typedef struct {
+  int t;              /* retained terms, 1 <= t <= tp                                 */
+  int tp;             /* projected size t_p                                           */
+  double beta;        /* depth-weighting exponent (0.8 gravity, 1.4 magnetic, Sec. 3) */
+  double lam;         /* focusing norm (1: approximately L1, Sec. 2.2)                */
+  double eps2;        /* focusing parameter epsilon^2 (> 0)                           */
+  double lower, upper;/* bounds on the model                                          */
+  int kmax;           /* maximum number of IRLS iterations (>= 1)                     */
+  int chi2_stop;      /* nonzero: stop on Eq. (12)                                    */
+  int reorth;         /* tf_gkb: 0 = classical Gram-Schmidt twice, 1 = modified       */
+  const double* alphas; /* HOST, kmax entries, or NULL: fixed alpha^(k) (skips UPRE)  */
+} tf_irls_params;
+
+typedef struct {
+  int iterations;     /* iterations run                                               */
+  double* alpha;      /* HOST arrays of kmax entries (each may be NULL): alpha^(k),  */
+  double* chi2;       /*   chi^2 of m^(k), and seconds of iteration k                 */
+  double* seconds;
+} tf_irls_report;
+
+tf_status tf_gkb(tf_op* op, const tf_irls_params* params, const void* d_obs, const void* sigma,
+                 void* m_out, tf_irls_report* report, tf_stream stream);
+tf_status tf_rsvd(tf_op* op, const tf_irls_params* params, const void* d_obs, const void* sigma,
+                  const void* omega, void* m_out, tf_irls_report* report, tf_stream stream);
+
+/* Host helpers of the projected solves (no GPU involved; exported for tests).
+ *
+ * tf_tridiag_eig_first: eigenvalues of the symmetric tridiagonal matrix with diagonal
+ * d[0..n) and off-diagonal e[0..n-1) (e[i] couples i and i+1), by the implicit QL
+ * iteration with Wilkinson shifts, together with the first component of each unit
+ * eigenvector (the Golub-Welsch weights' square roots, up to sign).  Overwrites d with
+ * the eigenvalues (unordered) and writes first[0..n); e is destroyed (needs n entries).
+ * The GKB driver applies it to B B^T, whose eigenvalues are s_i^2 and whose eigenvectors'
+ * first components are the first row of U (Alg. 1).  Errors: TF_EINVAL, TF_ENOTCONV.
+ *
+ * tf_damped_bidiag_solve: y = argmin ||[B; alpha I] y - [b0 e_1; 0]|| for the lower
+ * bidiagonal (tp+1) x tp matrix B with diagonal gam[0..tp) and subdiagonal bet[0..tp)
+ * (B(j+1, j) = bet[j]), by Givens QR (the Tikhonov-filtered solution of Alg. 1 on all t_p
+ * terms).  Errors: TF_EINVAL. */
+tf_status tf_tridiag_eig_first(int n, double* d, double* e, double* first);
+tf_status tf_damped_bidiag_solve(int tp, const double* gam, const double* bet, double alpha,
+                                 double b0, double* y);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* tf_last_error(void);
 

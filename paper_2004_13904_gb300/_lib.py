@@ -28,6 +28,19 @@ class tf_grid(ctypes.Structure):
                 ("z_edges", ctypes.POINTER(ctypes.c_double)), ("station_z", ctypes.c_double)]
 
 
+class tf_irls_params(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int), ("tp", ctypes.c_int), ("beta", ctypes.c_double),
+                ("lam", ctypes.c_double), ("eps2", ctypes.c_double), ("lower", ctypes.c_double),
+                ("upper", ctypes.c_double), ("kmax", ctypes.c_int), ("chi2_stop", ctypes.c_int),
+                ("reorth", ctypes.c_int), ("alphas", ctypes.POINTER(ctypes.c_double))]
+
+
+class tf_irls_report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("alpha", ctypes.POINTER(ctypes.c_double)),
+                ("chi2", ctypes.POINTER(ctypes.c_double)),
+                ("seconds", ctypes.POINTER(ctypes.c_double))]
+
+
 class TFError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -64,6 +77,10 @@ SIGNATURES = {
     "tf_peak_probe": [c_int, P(ctypes.c_double), vp],
     "tf_rows_dot": [c_int, vp, i64, i64, i64, vp, vp, vp],
     "tf_rows_axpy": [c_int, vp, i64, i64, i64, vp, vp, vp],
+    "tf_gkb": [vp, P(tf_irls_params), vp, vp, vp, P(tf_irls_report), vp],
+    "tf_rsvd": [vp, P(tf_irls_params), vp, vp, vp, vp, P(tf_irls_report), vp],
+    "tf_tridiag_eig_first": [c_int, vp, vp, vp],
+    "tf_damped_bidiag_solve": [c_int, vp, vp, ctypes.c_double, ctypes.c_double, vp],
 }
 
 

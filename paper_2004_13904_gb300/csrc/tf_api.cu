@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/tf.h"
+#include "tf_driver.h"
 #include "tf_internal.h"
 
 using tfk::CT;
@@ -744,6 +745,34 @@ tf_status tf_peak_probe(tf_dtype dtype, double* tflops, tf_stream stream) {
 const char* tf_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+namespace tfk {
+
+tf_status op_info(const tf_op* op, OpInfo* out) {
+  if (check_op(op)) return TF_EINVAL;
+  out->dtype = op->dtype;
+  out->m = op->m();
+  out->n = op->n();
+  out->nx = op->nx;
+  out->ny = op->ny;
+  out->nz = op->nz;
+  out->z_edges = op->z_edges;
+  out->station_z = op->station_z;
+  out->device = op->device;
+  return TF_OK;
+}
+
+tf_status api_fail(tf_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+}  // namespace tfk
 
 // ---- forward product without any allocation --------------------------------------------
 //

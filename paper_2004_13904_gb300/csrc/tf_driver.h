@@ -1,0 +1,25 @@
+// Internal hooks of tf_api.cu used by the IRLS drivers (tf_irls.cu); not part of the ABI.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/tf.h"
+
+namespace tfk {
+
+struct OpInfo {
+  tf_dtype dtype;
+  int64_t m, n;
+  int nx, ny, nz;
+  std::vector<double> z_edges;  // nz + 1, z positive down
+  double station_z;
+  int device;
+};
+
+// The operator's sizes and geometry.
+tf_status op_info(const tf_op* op, OpInfo* out);
+// Sets the calling thread's last-error message (what tf_last_error returns) and returns st.
+tf_status api_fail(tf_status st, const char* fmt, ...);
+
+}  // namespace tfk

@@ -30,7 +30,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["IRLSOptions", "IRLSResult", "invert", "gkb_factor", "rsvd_factor",
+__all__ = ["IRLSOptions", "IRLSResult", "invert", "invert_native", "gkb_factor", "rsvd_factor",
            "upre_value", "choose_alpha"]
 
 _GOLD = (math.sqrt(5.0) - 1.0) / 2.0
@@ -358,3 +358,38 @@ def invert(op, grid, d_obs: torch.Tensor, sigma: torch.Tensor, opts: IRLSOptions
             break
     res.model = m1
     return res
+
+
+def invert_native(op, d_obs: torch.Tensor, sigma: torch.Tensor, opts: IRLSOptions,
+                  omega: Optional[torch.Tensor] = None) -> IRLSResult:
+    """The same inversion through the library's C drivers tf_gkb / tf_rsvd (the whole
+    IRLS loop runs below the C ABI; the depth weights come from the operator's grid)."""
+    n, m = op.n, op.m
+    d_obs = d_obs.to(op.dtype).contiguous()
+    sigma = sigma.to(op.dtype).contiguous()
+    out = torch.empty(n, dtype=op.dtype, device=op.device)
+    fixed = None
+    if opts.alphas is not None:
+        fixed = (ctypes.c_double * opts.kmax)(*[float(a) for a in opts.alphas[:opts.kmax]])
+    p = _lib.tf_irls_params(opts.t, opts.tp, opts.beta, opts.lam, opts.eps2, opts.lower,
+                            opts.upper, opts.kmax, 1 if opts.chi2_stop else 0,
+                            1 if opts.reorth == "mgs" else 0,
+                            ctypes.cast(fixed, ctypes.POINTER(ctypes.c_double)) if fixed else None)
+    alphas = (ctypes.c_double * opts.kmax)()
+    chi2 = (ctypes.c_double * opts.kmax)()
+    secs = (ctypes.c_double * opts.kmax)()
+    rep = _lib.tf_irls_report(0, alphas, chi2, secs)
+    L = _lib.lib()
+    dp = ctypes.c_void_p
+    if opts.solver == "gkb":
+        st = L.tf_gkb(op._h, ctypes.byref(p), dp(d_obs.data_ptr()), dp(sigma.data_ptr()),
+                      dp(out.data_ptr()), ctypes.byref(rep), _stream())
+    else:
+        if omega is None:
+            raise ValueError("the RSVD solver needs omega (t_p x m)")
+        om = omega.to(op.dtype).contiguous()
+        st = L.tf_rsvd(op._h, ctypes.byref(p), dp(d_obs.data_ptr()), dp(sigma.data_ptr()),
+                       dp(om.data_ptr()), dp(out.data_ptr()), ctypes.byref(rep), _stream())
+    _lib.check(st)
+    k = rep.iterations
+    return IRLSResult(out, list(alphas[:k]), list(chi2[:k]), list(secs[:k]))
