@@ -257,6 +257,26 @@ tf_status tf_gkb(tf_op* op, const tf_irls_params* params, const void* d_obs, con
 tf_status tf_rsvd(tf_op* op, const tf_irls_params* params, const void* d_obs, const void* sigma,
                   const void* omega, void* m_out, tf_irls_report* report, tf_stream stream);
 
+/* ---- batches of independent problems (uneven sizes) ------------------------------------
+ *
+ * A tf_batch groups `count` operators (any mix of grids, kinds and dtypes on the current
+ * device) whose block products are independent.  tf_batch_products computes, for every
+ * i < count with non-NULL pointers, D[i] = G_i X[i] and XT[i] = G_i^T Y[i] on B columns
+ * (X[i]: n_i x B with ld n_i, D[i]: m_i x B with ld m_i, Y[i]: m_i x B, XT[i]: n_i x B;
+ * DEVICE pointers of operator i's dtype), spreading the operators over `streams`
+ * internal streams forked from and joined back into `stream`, so that problems too small
+ * to fill the GPU run side by side.  With use_graph, the first call with a given
+ * (B, pointer arrays, operator workspaces) runs eagerly, the next records the forked
+ * launches as one CUDA graph, and later identical calls replay it (one launch); any
+ * change re-records.  Operators must not be used elsewhere while a batch call runs.
+ * The batch does not own the operators.  Errors: TF_EINVAL, TF_ENOMEM, TF_ECUDA, and
+ * the products' errors.  (Batched products of many problems, App. A applied per problem.) */
+typedef struct tf_batch tf_batch;
+tf_status tf_batch_create(tf_op* const* ops, int count, int streams, tf_batch** out);
+tf_status tf_batch_destroy(tf_batch* batch);
+tf_status tf_batch_products(tf_batch* batch, int64_t B, const void* const* X, void* const* D,
+                            const void* const* Y, void* const* XT, int use_graph, tf_stream stream);
+
 /* Host helpers of the projected solves (no GPU involved; exported for tests).
  *
  * tf_tridiag_eig_first: eigenvalues of the symmetric tridiagonal matrix with diagonal

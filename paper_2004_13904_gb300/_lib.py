@@ -80,6 +80,9 @@ SIGNATURES = {
     "tf_gkb": [vp, P(tf_irls_params), vp, vp, vp, P(tf_irls_report), vp],
     "tf_rsvd": [vp, P(tf_irls_params), vp, vp, vp, vp, P(tf_irls_report), vp],
     "tf_tridiag_eig_first": [c_int, vp, vp, vp],
+    "tf_batch_create": [P(vp), c_int, c_int, P(vp)],
+    "tf_batch_destroy": [vp],
+    "tf_batch_products": [vp, i64, P(vp), P(vp), P(vp), P(vp), c_int, vp],
     "tf_damped_bidiag_solve": [c_int, vp, vp, ctypes.c_double, ctypes.c_double, vp],
 }
 

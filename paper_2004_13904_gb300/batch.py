@@ -14,7 +14,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
-__all__ = ["ProblemBatch", "tune", "TUNE_CACHE"]
+__all__ = ["ProblemBatch", "NativeBatch", "tune", "TUNE_CACHE"]
 
 
 class ProblemBatch:
@@ -73,6 +73,47 @@ class ProblemBatch:
         if self.graph is None:
             raise RuntimeError("capture() first")
         self.graph.replay()
+
+
+class NativeBatch:
+    """The same batch through the C ABI (tf_batch_create / tf_batch_products): the library
+    forks the operators' products over its own streams and, with use_graph, records them
+    once as a CUDA graph and replays it while pointers and operator set-ups are unchanged."""
+
+    def __init__(self, ops: Sequence, streams: int = 8):
+        import ctypes
+        from . import _lib
+        self.ops = list(ops)
+        self._ctypes, self._libm = ctypes, _lib
+        arr = (ctypes.c_void_p * len(self.ops))(*[op._h for op in self.ops])
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib().tf_batch_create(arr, len(self.ops), streams, ctypes.byref(h)))
+        self._h = h
+
+    def products(self, columns: int, X=None, D=None, Y=None, XT=None, use_graph: bool = True):
+        """D[i] = G_i X[i] and XT[i] = G_i^T Y[i] (blocks of `columns` rows, row-major like
+        Operator.matmat); None skips a direction."""
+        ct = self._ctypes
+        n = len(self.ops)
+
+        def ptrs(ts):
+            if ts is None:
+                return None
+            return (ct.c_void_p * n)(*[t.data_ptr() for t in ts])
+        stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+        self._libm.check(self._libm.lib().tf_batch_products(
+            self._h, columns, ptrs(X), ptrs(D), ptrs(Y), ptrs(XT), 1 if use_graph else 0, stream))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._libm.lib().tf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # (n1, n2, nz, dtype, columns) -> (engine, chunk)

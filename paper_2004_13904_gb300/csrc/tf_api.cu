@@ -762,6 +762,10 @@ tf_status op_info(const tf_op* op, OpInfo* out) {
   return TF_OK;
 }
 
+OpLaunchKey op_launch_key(const tf_op* op) {
+  return OpLaunchKey{op->w1, op->chunk, op->engine, op->rows_tile, op->cols_tile};
+}
+
 tf_status api_fail(tf_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;

@@ -19,6 +19,18 @@ struct OpInfo {
 
 // The operator's sizes and geometry.
 tf_status op_info(const tf_op* op, OpInfo* out);
+// Identity of the operator's launch configuration: its workspace address and column
+// chunk, its engine and tiles (a CUDA graph of its products is valid while these hold).
+struct OpLaunchKey {
+  const void* w1;
+  int64_t chunk;
+  int engine, rows_tile, cols_tile;
+  bool operator==(const OpLaunchKey& o) const {
+    return w1 == o.w1 && chunk == o.chunk && engine == o.engine && rows_tile == o.rows_tile &&
+           cols_tile == o.cols_tile;
+  }
+};
+OpLaunchKey op_launch_key(const tf_op* op);
 // Sets the calling thread's last-error message (what tf_last_error returns) and returns st.
 tf_status api_fail(tf_status st, const char* fmt, ...);
 

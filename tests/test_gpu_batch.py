@@ -64,3 +64,44 @@ def test_tuner_choice_keeps_results():
     assert engine in (0, 1) and 1 <= chunk <= 7
     assert (op.n1, op.n2, op.nz, str(op.dtype), 7) in TUNE_CACHE
     assert torch.allclose(op.matmat(X), ref, rtol=0, atol=1e-12 * ref.abs().max())
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_native_batch_matches_single_products(use_graph):
+    # tf_batch_products, eager and recorded/replayed, equals each operator's own products;
+    # new output pointers make the batch record again
+    import torch
+    from paper_2004_13904_gb300.batch import NativeBatch
+    ops = _ops(torch.float32, 5)
+    cols = 4
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    X = [torch.randn(cols, op.n, generator=gen, device="cuda") for op in ops]
+    Y = [torch.randn(cols, op.m, generator=gen, device="cuda") for op in ops]
+    ref_D = [op.matmat(x) for op, x in zip(ops, X)]
+    ref_XT = [op.rmatmat(y) for op, y in zip(ops, Y)]
+    b = NativeBatch(ops, streams=3)
+    for outs in range(2):
+        D = [torch.full((cols, op.m), float("nan"), device="cuda") for op in ops]
+        XT = [torch.full((cols, op.n), float("nan"), device="cuda") for op in ops]
+        for _ in range(3):          # eager, record + launch, replay
+            for t in D + XT:
+                t.fill_(float("nan"))
+            b.products(cols, X, D, Y, XT, use_graph=use_graph)
+            torch.cuda.synchronize()
+            for a, r in zip(D + XT, ref_D + ref_XT):
+                assert torch.equal(a, r)
+    # one direction only
+    D = [torch.zeros(cols, op.m, device="cuda") for op in ops]
+    b.products(cols, X=X, D=D, use_graph=use_graph)
+    torch.cuda.synchronize()
+    for a, r in zip(D, ref_D):
+        assert torch.equal(a, r)
+    b.close()
+
+
+def test_native_batch_rejects_bad_arguments():
+    import ctypes
+    from paper_2004_13904_gb300 import _lib
+    L = _lib.lib()
+    h = ctypes.c_void_p()
+    assert L.tf_batch_create(None, 0, 1, ctypes.byref(h)) == _lib.TF_EINVAL
