@@ -66,9 +66,29 @@ template <typename T> constexpr int cols_min_blocks(int nt, int threads_per_sm) 
 template <typename T> constexpr int kFwdThreadsPerSM = 512;
 template <typename T> constexpr int kAdjThreadsPerSM = 640;
 
+// Visits every (element index n < E, pair group q < TP) once.  When E fills at least 4/5
+// of the CTA's threads, each thread takes whole element indices and loops over the pair
+// groups (the swizzled row position and the element's own index arithmetic are shared by
+// the TP accesses); otherwise a flat walk over all pairs keeps the threads busy.
+template <int NT, int TP, class Body>
+__device__ __forceinline__ void visit_pairs(int E, const Body& body) {
+  const int full = (E + NT - 1) / NT * NT;
+  if (5 * E >= 4 * full) {
+    for (int n = threadIdx.x; n < E; n += NT)
+#pragma unroll
+      for (int q = 0; q < TP; ++q) body(n, q);
+  } else {
+    for (int u = threadIdx.x; u < TP * E; u += NT) {
+      const int q = u / E;
+      body(u - q * E, q);
+    }
+  }
+}
+
 // The row kernels stage and unpack two adjacent sequences (2q, 2q + 1) per thread and
 // element: one 16-byte shared-memory access (the pair is adjacent in the swizzled
-// buffer), and the four real rows 2 (pair0 + 2q) + 0..3 that feed them.
+// buffer), and the four real rows 2 (pair0 + 2q) + 0..3 that feed them.  The loops
+// over (element, pair group) go through visit_pairs.
 // ZHI: the rows' data lies in [0, N/2) of the sequence, so staging fills only that half
 // and the first pass takes the upper half as zero.
 template <typename T, class P, int TB, int V, int NT, bool ZHI>
@@ -85,10 +105,10 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
   const int src_ext = nrows * len;
   const T* scale = a.scale;
   constexpr int NS = ZHI && P::can_zero_hi ? N / 2 : N;   // staged rows of the buffer
-  for (int u = threadIdx.x; u < TP * NS; u += NT) {
-    const int q = u / NS, n = u - q * NS;
-    const int r0 = 2 * (pair0 + 2 * q);
+  visit_pairs<NT, TP>(NS, [&](int n, int q) {
+    const ct::RowAt<C, TB> ra(n);
     const int e = n - off;
+    const int r0 = 2 * (pair0 + 2 * q);
     T x[4] = {T(0), T(0), T(0), T(0)};
     if (e >= 0 && e < len) {
 #pragma unroll
@@ -100,20 +120,20 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
       }
     }
     const C v[2] = {mk<C>(x[0], x[1]), mk<C>(x[2], x[3])};
-    const int p = ct::at<C, TB>(n, 2 * q);
+    const int p = ra(2 * q);
     if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::st(buf + p, v);
-  }
+  });
   __syncthreads();
   const ct::Buf<C, TB, V> b{buf, N * TB};
   P::template run<TB, V, NT, false, ZHI>(tw, buf, b, b);
   C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int hs = a.hs, dst_ext = nrows * hs;
-  for (int u = threadIdx.x; u < TP * NH; u += NT) {
-    const int q = u / NH, k = u - q * NH;
+  visit_pairs<NT, TP>(NH, [&](int k, int q) {
     const int r0 = 2 * (pair0 + 2 * q);
-    if (r0 >= nrows) continue;
+    if (r0 >= nrows) return;
+    const ct::RowAt<C, TB> rk(k), rc(k ? N - k : 0);
     C z[2], zc[2];
-    const int pk = ct::at<C, TB>(k, 2 * q), pc = ct::at<C, TB>(k ? N - k : 0, 2 * q);
+    const int pk = rk(2 * q), pc = rc(2 * q);
     if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::ld(buf + pk, z);
     if (TF_IN(kSiteSmem + 3, pc + 1, N * TB)) Vec<2, C>::ld(buf + pc, zc);
 #pragma unroll
@@ -126,7 +146,7 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
       if (rb < nrows && TF_IN(kSiteR2cDst, rb * hs + k, dst_ext))
         dst[rb * hs + k] = mk<C>(T(0.5) * (z[h].y - zc[h].y), T(-0.5) * (z[h].x - zc[h].x));
     }
-  }
+  });
 }
 
 template <typename T, class P, int TB, int V, int NT>
@@ -141,8 +161,8 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
   const int nrows = a.nrows;
   const C* src = a.src + (int64_t)blockIdx.y * a.src_ld;
   const int hs = a.hs, src_ext = nrows * hs;
-  for (int u = threadIdx.x; u < TP * NH; u += NT) {
-    const int q = u / NH, k = u - q * NH;
+  visit_pairs<NT, TP>(NH, [&](int k, int q) {
+    const bool self = (k == 0) || (2 * k == N);
     const int r0 = 2 * (pair0 + 2 * q);
     C x[4];
 #pragma unroll
@@ -150,7 +170,6 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
       x[i] = zero<C>();
       if (r0 + i < nrows && TF_IN(kSiteC2rSrc, (r0 + i) * hs + k, src_ext)) x[i] = src[(r0 + i) * hs + k];
     }
-    const bool self = (k == 0) || (2 * k == N);
     C lo[2], hi[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -159,13 +178,13 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
       lo[h] = mk<C>(xa.x - xb.y, xa.y + xb.x);
       hi[h] = mk<C>(xa.x + xb.y, xb.x - xa.y);
     }
-    const int pk = ct::at<C, TB>(k, 2 * q);
+    const int pk = ct::RowAt<C, TB>(k)(2 * q);
     if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::st(buf + pk, lo);
     if (!self) {
-      const int pc = ct::at<C, TB>(N - k, 2 * q);
+      const int pc = ct::RowAt<C, TB>(N - k)(2 * q);
       if (TF_IN(kSiteSmem + 3, pc + 1, N * TB)) Vec<2, C>::st(buf + pc, hi);
     }
-  }
+  });
   __syncthreads();
   const ct::Buf<C, TB, V> b{buf, N * TB};
   P::template run<TB, V, NT, true>(tw, buf, b, b);
@@ -173,12 +192,11 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
   const int L = a.out_len, off = a.seq_off;
   const int dst_ext = nrows * L;
   const T* scale = a.scale;
-  for (int u = threadIdx.x; u < TP * L; u += NT) {
-    const int q = u / L, i = u - q * L;
+  visit_pairs<NT, TP>(L, [&](int i, int q) {
     const int r0 = 2 * (pair0 + 2 * q);
-    if (r0 >= nrows) continue;
+    if (r0 >= nrows) return;
     C z[2];
-    const int p = ct::at<C, TB>(off + i, 2 * q);
+    const int p = ct::RowAt<C, TB>(off + i)(2 * q);
     if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::ld(buf + p, z);
     const T y[4] = {z[0].x, z[0].y, z[1].x, z[1].y};
 #pragma unroll
@@ -188,7 +206,7 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
       if (TF_IN(kSiteC2rDst, o, dst_ext))
         dst[o] = (scale && TF_IN(kSiteC2rScale, o, dst_ext)) ? y[j] * scale[o] : y[j];
     }
-  }
+  });
 }
 
 // Spectrum values are staged in registers ahead of use in single precision only (the
@@ -196,9 +214,9 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
 template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::value;
 
 // Column stage of G x (ZHI: ny <= N/2, the layer rows fill the lower half).  In single
-// precision each thread loads the spectrum values that
-// its last forward pass multiplies at the start of every layer, into registers, so that
-// their global-memory latency overlaps the layer's first passes.
+// precision each thread loads the spectrum values that its last forward pass multiplies
+// at the start of every layer, into registers, so that their global-memory latency
+// overlaps the layer's first passes.
 template <typename T, class P, int TB, int V, int NT, bool ZHI>
 __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>)) k_cols_fwd(const ColsFwd<T> a) {
   typedef typename CT<T>::C C;

@@ -68,6 +68,17 @@ template <typename C, int TB> __host__ __device__ __forceinline__ int at(int idx
   return row * TB + (b ^ swz<C, TB>(row));
 }
 
+// at(idx, b) for a fixed idx and varying even b: the row's base and swizzle computed once.
+template <typename C, int TB> struct RowAt {
+  int base, sw;
+  __device__ __forceinline__ explicit RowAt(int idx) {
+    const int row = row_of<C, TB>(idx);
+    base = row * TB;
+    sw = swz<C, TB>(row);
+  }
+  __device__ __forceinline__ int operator()(int b) const { return base + (b ^ sw); }
+};
+
 // The working buffer: [N][TB] complex, sequence index fastest (swizzled).
 template <typename C, int TB, int V> struct Buf {
   static constexpr bool kIsBuf = true;
