@@ -58,13 +58,14 @@ __device__ __forceinline__ void ld_row_vec(const C* p, int k1, int nh, bool ok, 
 // Register budgets of the column kernels, as a minimum number of resident CTAs per SM
 // for __launch_bounds__ (measured with 1260-column blocks at transform lengths 64 to
 // 512: the single-precision forward kernel is fastest near 128 registers a thread, the
-// adjoint near 100; the double kernels are indifferent).  The row kernels keep the compiler's
+// adjoint near 100, and near 85 at n >= 448; the double kernels are indifferent).  The row kernels keep the compiler's
 // default budget, which measured fastest for them.
 template <typename T> constexpr int cols_min_blocks(int nt, int threads_per_sm) {
   return std::is_same<T, float>::value && threads_per_sm / nt > 1 ? threads_per_sm / nt : 1;
 }
 template <typename T> constexpr int kFwdThreadsPerSM = 512;
-template <typename T> constexpr int kAdjThreadsPerSM = 640;
+// the adjoint at n >= 448 (256 threads per CTA) measured fastest with a tighter budget
+template <typename T, int N> constexpr int kAdjThreadsPerSM = N >= 448 ? 768 : 640;
 
 // Visits every (element index n < E, pair group q < TP) once.  When E fills at least 4/5
 // of the CTA's threads, each thread takes whole element indices and loops over the pair
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>
 // Column stage of G^T y: forward transform of the data columns into shared memory, then
 // per layer the product with conj(G_r) and the inverse transform.
 template <typename T, class P, int TB, int V, int NT>
-__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kAdjThreadsPerSM<T>)) k_cols_adj(const ColsAdj<T> a) {
+__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kAdjThreadsPerSM<T, P::n>)) k_cols_adj(const ColsAdj<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
