@@ -307,7 +307,12 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
   {
     std::vector<int> rad;
     if ((op->ct1 = ct_radices(op->n1, rad))) op->p1ct = make_plan_from(op->n1, rad);
-    if ((op->ct2 = ct_radices(op->n2, rad))) op->p2ct = make_plan_from(op->n2, rad);
+    if ((op->ct2 = ct_radices(op->n2, rad))) {
+      int r[tfk::kMaxPass];  // single-precision column kernels have their own menu
+      const int np = dt == TF_F32 ? tfk::ct_menu_cols_radices(op->n2, r) : 0;
+      if (np > 0) rad.assign(r, r + np);
+      op->p2ct = make_plan_from(op->n2, rad);
+    }
   }
   op->rows_tile = dt == TF_F32 ? 8 : 4;
   op->cols_tile = dt == TF_F32 ? 8 : 4;

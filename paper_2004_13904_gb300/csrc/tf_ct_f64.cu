@@ -3,5 +3,5 @@
 
 namespace tfk {
 TF_DEFINE_OOB_READER(oob_read_ct_f64)
-TF_CT_DEFINE_DISPATCH(double)
+TF_CT_DEFINE_DISPATCH(double, TF_CT_MENU)
 }  // namespace tfk

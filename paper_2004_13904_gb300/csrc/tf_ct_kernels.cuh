@@ -25,6 +25,13 @@
   X(448, 8, 8, 7)            \
   X(512, 8, 8, 8)
 
+// The column kernels' menu in single precision: n = 224 as two passes (16, 14), which
+// moves each value through shared memory one time fewer than (8, 4, 7); the double
+// kernels keep TF_CT_MENU (measured 2 % slower with the two-pass plan).
+#define TF_CT_MENU_COLS_F32(X)                                                              \
+  X(32, 8, 4) X(64, 8, 8) X(96, 8, 4, 3) X(128, 8, 8, 2) X(160, 8, 4, 5) X(192, 8, 8, 3)    \
+  X(224, 16, 14) X(256, 8, 8, 4) X(320, 8, 8, 5) X(448, 8, 8, 7) X(512, 8, 8, 8)
+
 namespace tfk {
 namespace ctk {
 
@@ -64,6 +71,9 @@ template <typename T> constexpr int cols_min_blocks(int nt, int threads_per_sm) 
   return std::is_same<T, float>::value && threads_per_sm / nt > 1 ? threads_per_sm / nt : 1;
 }
 template <typename T> constexpr int kFwdThreadsPerSM = 512;
+// two-pass plans (first radix 16, 64-thread CTAs): about 170 registers (measured against
+// 320, 448 and 512 resident threads per SM)
+constexpr int kWideThreadsPerSM = 384;
 // the adjoint at n >= 448 (256 threads per CTA) measured fastest with a tighter budget
 template <typename T, int N> constexpr int kAdjThreadsPerSM = N >= 448 ? 768 : 640;
 
@@ -107,7 +117,7 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
   const T* scale = a.scale;
   constexpr int NS = ZHI && P::can_zero_hi ? N / 2 : N;   // staged rows of the buffer
   visit_pairs<NT, TP>(NS, [&](int n, int q) {
-    const ct::RowAt<C, TB> ra(n);
+    const ct::RowAt<C, TB, P::first_r> ra(n);
     const int e = n - off;
     const int r0 = 2 * (pair0 + 2 * q);
     T x[4] = {T(0), T(0), T(0), T(0)};
@@ -125,14 +135,14 @@ __global__ void __launch_bounds__(NT) k_rows_r2c(const RowsR2C<T> a) {
     if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::st(buf + p, v);
   });
   __syncthreads();
-  const ct::Buf<C, TB, V> b{buf, N * TB};
+  const ct::Buf<C, TB, V, P::first_r> b{buf, N * TB};
   P::template run<TB, V, NT, false, ZHI>(tw, buf, b, b);
   C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int hs = a.hs, dst_ext = nrows * hs;
   visit_pairs<NT, TP>(NH, [&](int k, int q) {
     const int r0 = 2 * (pair0 + 2 * q);
     if (r0 >= nrows) return;
-    const ct::RowAt<C, TB> rk(k), rc(k ? N - k : 0);
+    const ct::RowAt<C, TB, P::first_r> rk(k), rc(k ? N - k : 0);
     C z[2], zc[2];
     const int pk = rk(2 * q), pc = rc(2 * q);
     if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::ld(buf + pk, z);
@@ -179,15 +189,15 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
       lo[h] = mk<C>(xa.x - xb.y, xa.y + xb.x);
       hi[h] = mk<C>(xa.x + xb.y, xb.x - xa.y);
     }
-    const int pk = ct::RowAt<C, TB>(k)(2 * q);
+    const int pk = ct::RowAt<C, TB, P::first_r>(k)(2 * q);
     if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::st(buf + pk, lo);
     if (!self) {
-      const int pc = ct::RowAt<C, TB>(N - k)(2 * q);
+      const int pc = ct::RowAt<C, TB, P::first_r>(N - k)(2 * q);
       if (TF_IN(kSiteSmem + 3, pc + 1, N * TB)) Vec<2, C>::st(buf + pc, hi);
     }
   });
   __syncthreads();
-  const ct::Buf<C, TB, V> b{buf, N * TB};
+  const ct::Buf<C, TB, V, P::first_r> b{buf, N * TB};
   P::template run<TB, V, NT, true>(tw, buf, b, b);
   T* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int L = a.out_len, off = a.seq_off;
@@ -197,7 +207,7 @@ __global__ void __launch_bounds__(NT) k_rows_c2r(const RowsC2R<T> a) {
     const int r0 = 2 * (pair0 + 2 * q);
     if (r0 >= nrows) return;
     C z[2];
-    const int p = ct::RowAt<C, TB>(off + i)(2 * q);
+    const int p = ct::RowAt<C, TB, P::first_r>(off + i)(2 * q);
     if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::ld(buf + p, z);
     const T y[4] = {z[0].x, z[0].y, z[1].x, z[1].y};
 #pragma unroll
@@ -219,7 +229,7 @@ template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::val
 // at the start of every layer, into registers, so that their global-memory latency
 // overlaps the layer's first passes.
 template <typename T, class P, int TB, int V, int NT, bool ZHI>
-__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>)) k_cols_fwd(const ColsFwd<T> a) {
+__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? kWideThreadsPerSM : kFwdThreadsPerSM<T>)) k_cols_fwd(const ColsFwd<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n;
   constexpr bool kPre = kSpecPrefetch<T>;
@@ -299,7 +309,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kFwdThreadsPerSM<T>
 // Column stage of G^T y: forward transform of the data columns into shared memory, then
 // per layer the product with conj(G_r) and the inverse transform.
 template <typename T, class P, int TB, int V, int NT>
-__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, kAdjThreadsPerSM<T, P::n>)) k_cols_adj(const ColsAdj<T> a) {
+__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? kWideThreadsPerSM : kAdjThreadsPerSM<T, P::n>)) k_cols_adj(const ColsAdj<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -379,6 +389,14 @@ cudaError_t launch_k(const A& a, dim3 grid, int nt, size_t sm, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Column kernels' tiles: those of the length, except for plans starting with radix 16
+// (two passes), which have half the butterfly tasks per pass: 8 sequences per CTA on 64
+// threads (measured against 16 sequences on 128 threads: 2.52 vs 2.75 ms per c2 step).
+template <typename T, class P, bool WIDE = (P::first_r >= 16)> struct ColTiles : Tiles<T, P::n> {};
+template <typename T, class P> struct ColTiles<T, P, true> {
+  static constexpr int TB = 8, V = 2, NT = 64;
+};
+
 template <typename T, class P>
 cudaError_t rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
@@ -400,7 +418,7 @@ cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
 }
 template <typename T, class P>
 cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
-  typedef Tiles<T, P::n> TL;
+  typedef ColTiles<T, P> TL;
   const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
   const dim3 grid(cdiv(a.nh, TL::TB), ncols);
   if (P::can_zero_hi && a.ny <= P::n / 2)
@@ -409,7 +427,7 @@ cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
 }
 template <typename T, class P>
 cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
-  typedef Tiles<T, P::n> TL;
+  typedef ColTiles<T, P> TL;
   constexpr auto k = k_cols_adj<T, P, TL::TB, TL::V, TL::NT>;
   const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
   cudaError_t e = set_smem<k>(sm);
@@ -425,7 +443,7 @@ cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
 #define TF_CT_FIRST(x, ...) x
 
 // Defines the dtype's four dispatchers: cudaErrorNotSupported for lengths off the menu.
-#define TF_CT_DEFINE_DISPATCH(TYPE)                                                        \
+#define TF_CT_DEFINE_DISPATCH(TYPE, COLS_MENU)                                             \
   template <>                                                                              \
   cudaError_t ct_rows_r2c<TYPE>(const RowsR2C<TYPE>& a, int ncols, cudaStream_t s) {       \
     typedef TYPE T;                                                                        \
@@ -446,7 +464,7 @@ cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
   cudaError_t ct_cols_fwd<TYPE>(const ColsFwd<TYPE>& a, int ncols, cudaStream_t s) {       \
     typedef TYPE T;                                                                        \
     switch (a.plan.n) {                                                                    \
-      TF_CT_MENU(TF_CT_FWD_CASE)                                                           \
+      COLS_MENU(TF_CT_FWD_CASE)                                                            \
       default: return cudaErrorNotSupported;                                               \
     }                                                                                      \
   }                                                                                        \
@@ -454,7 +472,7 @@ cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
   cudaError_t ct_cols_adj<TYPE>(const ColsAdj<TYPE>& a, int ncols, cudaStream_t s) {       \
     typedef TYPE T;                                                                        \
     switch (a.plan.n) {                                                                    \
-      TF_CT_MENU(TF_CT_ADJ_CASE)                                                           \
+      COLS_MENU(TF_CT_ADJ_CASE)                                                            \
       default: return cudaErrorNotSupported;                                               \
     }                                                                                      \
   }

@@ -57,22 +57,22 @@ template <typename C, int TB> __host__ __device__ constexpr int swz(int row) {
   return TB >= 4 ? ((row / rows_per_line) & (TB / 2 - 1)) << 1 : 0;
 }
 // Rows of 64 bytes fill half of the 32 banks, the half given by the row's parity.  The
-// first pass of every plan is radix 8 and stores rows idx and idx + 8 in the same
-// quarter-warp phase; swapping the rows of each even/odd pair in every other block of 8
+// first pass of a plan with first radix S stores rows idx and idx + S in the same
+// quarter-warp phase; swapping the rows of each even/odd pair in every other block of S
 // puts those two in different halves.  (A permutation of [0, N) for even N.)
-template <typename C, int TB> __host__ __device__ constexpr int row_of(int idx) {
-  return TB * sizeof(C) == 64 ? idx ^ ((idx >> 3) & 1) : idx;
+template <typename C, int TB, int S = 8> __host__ __device__ constexpr int row_of(int idx) {
+  return TB * sizeof(C) == 64 ? idx ^ ((idx / S) & 1) : idx;
 }
-template <typename C, int TB> __host__ __device__ __forceinline__ int at(int idx, int b) {
-  const int row = row_of<C, TB>(idx);
+template <typename C, int TB, int S = 8> __host__ __device__ __forceinline__ int at(int idx, int b) {
+  const int row = row_of<C, TB, S>(idx);
   return row * TB + (b ^ swz<C, TB>(row));
 }
 
 // at(idx, b) for a fixed idx and varying even b: the row's base and swizzle computed once.
-template <typename C, int TB> struct RowAt {
+template <typename C, int TB, int S = 8> struct RowAt {
   int base, sw;
   __device__ __forceinline__ explicit RowAt(int idx) {
-    const int row = row_of<C, TB>(idx);
+    const int row = row_of<C, TB, S>(idx);
     base = row * TB;
     sw = swz<C, TB>(row);
   }
@@ -80,16 +80,16 @@ template <typename C, int TB> struct RowAt {
 };
 
 // The working buffer: [N][TB] complex, sequence index fastest (swizzled).
-template <typename C, int TB, int V> struct Buf {
+template <typename C, int TB, int V, int S = 8> struct Buf {
   static constexpr bool kIsBuf = true;
   C* p;
   int ext;  // elements of the buffer (checked builds test every access against it)
   __device__ __forceinline__ void operator()(int idx, int b0, C* o) const {
-    const int e = at<C, TB>(idx, b0);
+    const int e = at<C, TB, S>(idx, b0);
     if (TF_IN(kSiteSmem, e + V - 1, ext) && TF_IN(kSiteSmem, e, ext)) Vec<V, C>::ld(p + e, o);
   }
   __device__ __forceinline__ void operator()(int idx, int b0, const C* v, int) const {
-    const int e = at<C, TB>(idx, b0);
+    const int e = at<C, TB, S>(idx, b0);
     if (TF_IN(kSiteSmem, e + V - 1, ext) && TF_IN(kSiteSmem, e, ext)) Vec<V, C>::st(p + e, v);
   }
 };
@@ -207,16 +207,16 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
 // `last`, the others use the shared buffer.  Twiddle layout as in FftPlan.
 template <int N, int Ns, int TwOff, int... Rs> struct Run;
 template <int N, int Ns, int TwOff, int R, int... Rest> struct Run<N, Ns, TwOff, R, Rest...> {
-  template <int TB, int V, int NT, bool INV, bool FIRST, bool ZHI, typename C, class L0, class SL>
+  template <int TB, int V, int NT, bool INV, bool FIRST, bool ZHI, int S, typename C, class L0, class SL>
   static __device__ __forceinline__ void go(const C* tw, C* buf, const L0& first, const SL& last) {
     constexpr bool LAST = sizeof...(Rest) == 0;
-    const Buf<C, TB, V> b{buf, N * TB};
+    const Buf<C, TB, V, S> b{buf, N * TB};
     if constexpr (FIRST && LAST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, last);
     else if constexpr (FIRST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, b);
     else if constexpr (LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, last);
     else pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, b);
     if constexpr (!LAST)
-      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false, false>(
+      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false, false, S>(
           tw, buf, first, last);
   }
 };
@@ -236,10 +236,11 @@ template <int N, int... Rs> struct Plan {
   static constexpr int last_ns = LastOf<Rs...>::prod_before;  // its stride
   // The upper half of the input may be declared zero (run<..., ZHI = true>) when the
   // first radix is even.
-  static constexpr bool can_zero_hi = FirstOf<Rs...>::r % 2 == 0;
+  static constexpr int first_r = FirstOf<Rs...>::r;        // radix of the first pass
+  static constexpr bool can_zero_hi = first_r % 2 == 0;
   template <int TB, int V, int NT, bool INV, bool ZHI = false, typename C, class L0, class SL>
   static __device__ __forceinline__ void run(const C* tw, C* buf, const L0& first, const SL& last) {
-    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi>(tw, buf, first, last);
+    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r>(tw, buf, first, last);
   }
 };
 

@@ -88,6 +88,8 @@ template <> cudaError_t ct_cols_adj<double>(const ColsAdj<double>&, int, cudaStr
 int ct_menu_count();
 int ct_menu_length(int i);
 int ct_menu_radices(int i, int* radices /* up to kMaxPass */);
+// radix list of the single-precision column kernels' plan for length n (0 when n has none)
+int ct_menu_cols_radices(int n, int* radices /* up to kMaxPass */);
 
 // Bounds-check records of each kernel translation unit (false in unchecked builds).
 bool oob_read_generic(OobRecord* out, bool clear);
