@@ -239,6 +239,10 @@ tf_status alloc_workspace(tf_op* op, int64_t chunk) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
   e = cudaMalloc(&op->w2, (size_t)chunk * op->w2_per_col() * op->csize() + guard);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+  // zero once: the row padding (values nh..hs-1) is never written by the row kernels
+  e = cudaMemset(op->w1, 0, (size_t)chunk * op->w1_per_col() * op->csize() + guard);
+  if (e == cudaSuccess) e = cudaMemset(op->w2, 0, (size_t)chunk * op->w2_per_col() * op->csize() + guard);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(workspace)");
   op->chunk = chunk;
   return TF_OK;
 }

@@ -44,9 +44,9 @@ template <typename C> __device__ __forceinline__ C zero() { return mk<C>(0, 0); 
 // Half-spectrum rows are stored with a row stride hs that is a multiple of 16 values,
 // so the V values k1 .. k1+V-1 (k1 a multiple of V) of a row are one aligned vector.
 // Values at k1 + q >= nh lie in the row's padding: stored freely, and loaded as zero
-// with MASK (workspace rows, whose padding is never written).  The layer spectra are
-// zero in their padding, so their loads skip the mask, which would otherwise make the
-// load complete at the point of issue.
+// with MASK.  Buffers whose padding is known to be zero (the layer spectra, and the
+// workspace rows read by cols_fwd) skip the mask, whose select would otherwise make
+// the load complete at the point of issue.
 template <int V, bool MASK, typename C>
 __device__ __forceinline__ void ld_row_vec(const C* p, int k1, int nh, bool ok, C* o) {
   if (ok) {
@@ -264,15 +264,14 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
       }
     }
     const bool first_layer = (r == 0);
-    // (one load per value: a vector load here measured slower, unlike in cols_adj)
+    // Row-transformed layers as aligned vectors without a padding mask: the workspace is
+    // zeroed when allocated, the row kernels never write its padding, and the column
+    // kernels write zeros there (their padded sequences have zero inputs).  A masked load
+    // measured much slower here (the mask's select waits for the load).
     auto load = [=](int idx, int b0, C* o) {
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const int k1 = k0 + b0 + q;
-        const int e = zoff + idx * hs + k1;
-        o[q] = zero<C>();
-        if (idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e, z_ext)) o[q] = z[e];
-      }
+      const int k1 = k0 + b0;
+      const int e = zoff + idx * hs + k1;
+      ld_row_vec<V, false>(z + e, k1, nh, idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e + V - 1, z_ext), o);
     };
     auto mac = [&](int idx, int b0, const C* v, int slot) {
       C cur[V];
