@@ -332,7 +332,10 @@ def main():
         "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": WORKLOAD, "block_columns": cols_per_rank, "fft": [op.n1, op.n2],
                    "tuning": list(op.tuning()),
-                   "l2": "inputs (X 610 MB, Y 50 MB in FP32) exceed L2; no flush"},
+                   "l2": (f"inputs (X {g.n * cols_per_rank * esz / 1e6:.0f} MB, "
+                          f"Y {g.m * cols_per_rank * esz / 1e6:.0f} MB) "
+                          + ("exceed L2; no flush" if g.n * cols_per_rank * esz > 129e6 else
+                             "fit in L2"))},
         "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
         "hbm_algorithmic_gbs": hbm_alg, "stage_share": stage_share, "clocks": clk,
     }
