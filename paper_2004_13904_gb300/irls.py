@@ -370,6 +370,8 @@ def invert_native(op, d_obs: torch.Tensor, sigma: torch.Tensor, opts: IRLSOption
     out = torch.empty(n, dtype=op.dtype, device=op.device)
     fixed = None
     if opts.alphas is not None:
+        if len(opts.alphas) < opts.kmax:
+            raise ValueError(f"alphas has {len(opts.alphas)} entries, kmax is {opts.kmax}")
         fixed = (ctypes.c_double * opts.kmax)(*[float(a) for a in opts.alphas[:opts.kmax]])
     p = _lib.tf_irls_params(opts.t, opts.tp, opts.beta, opts.lam, opts.eps2, opts.lower,
                             opts.upper, opts.kmax, 1 if opts.chi2_stop else 0,
