@@ -48,7 +48,7 @@ typedef enum {
   TF_EINVAL = 1,        /* invalid argument (null pointer, bad size, bad geometry)   */
   TF_ENOMEM = 2,        /* device allocation failed                                  */
   TF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed               */
-  TF_EUNSUPPORTED = 4,  /* valid but outside what this build supports (FFT size)     */
+  TF_EUNSUPPORTED = 4,  /* valid but outside what the library supports (FFT size)   */
   TF_ENOTCONV = 5,      /* reserved for iterative drivers                            */
   TF_ETIMEOUT = 6       /* reserved for bounded device-side waits                    */
 } tf_status;
