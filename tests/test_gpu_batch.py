@@ -105,3 +105,29 @@ def test_native_batch_rejects_bad_arguments():
     L = _lib.lib()
     h = ctypes.c_void_p()
     assert L.tf_batch_create(None, 0, 1, ctypes.byref(h)) == _lib.TF_EINVAL
+
+
+def test_native_batch_rerecords_after_operator_change():
+    # a recorded graph holds the operators' workspaces; changing one operator's chunk
+    # (which reallocates its workspace) must make the batch record again, not replay
+    import torch
+    from paper_2004_13904_gb300.batch import NativeBatch
+    ops = _ops(torch.float32, 3)
+    cols = 6
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    X = [torch.randn(cols, op.n, generator=gen, device="cuda") for op in ops]
+    ref = [op.matmat(x) for op, x in zip(ops, X)]
+    D = [torch.empty(cols, op.m, device="cuda") for op in ops]
+    b = NativeBatch(ops, streams=2)
+    for _ in range(3):              # eager, record + launch, replay
+        b.products(cols, X=X, D=D)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, r) for a, r in zip(D, ref))
+    ops[1].set_tuning(0, 0, 2)      # new chunk: new workspace
+    for _ in range(3):
+        for t in D:
+            t.fill_(float("nan"))
+        b.products(cols, X=X, D=D)
+        torch.cuda.synchronize()
+        assert all(torch.equal(a, r) for a, r in zip(D, ref))
+    b.close()
