@@ -1,0 +1,123 @@
+"""Shared-memory layout of the compile-time FFT engine (host logic, no GPU).
+
+The kernels keep TB sequences of length N in one [N][TB] buffer with the swizzled
+position at(idx, b) of tf_fft_ct.cuh: 64-byte rows are paired across blocks of S rows
+(S = the plan's first radix) and the sequence index is XOR-swizzled by the row.  This test
+restates that mapping and the Stockham pass index map in Python.  It then checks two
+properties for every plan of the menus in tf_ct_kernels.cuh:
+
+* at() is a bijection onto [0, N*TB) (both precisions);
+* every pass's loads and stores (16-byte accesses by quarter-warp phases, FP32 tiles)
+  need the minimum number of shared-memory wavefronts, i.e. no bank conflicts.
+
+The menus are parsed from the kernel header, so a new plan is covered automatically.
+"""
+import os
+import re
+from collections import defaultdict
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "paper_2004_13904_gb300", "csrc", "tf_ct_kernels.cuh")
+
+
+def _menu(name):
+    text = open(HDR).read()
+    i = text.index(f"#define {name}(X)")
+    j = text.index("\n\n", i)
+    return [tuple(int(v) for v in m.split(",")) for m in re.findall(r"X\(([\d,\s]+)\)", text[i:j])]
+
+
+def _plans():
+    out = []
+    for name in ("TF_CT_MENU", "TF_CT_MENU_COLS_F32"):
+        for entry in _menu(name):
+            out.append((name, entry[0], entry[1:]))
+    return out
+
+
+def _tiles(N, radices, dtype):
+    """(TB, V, NT) as Tiles / ColTiles choose them."""
+    if radices[0] >= 16:
+        return 8, 2, 64
+    if dtype == "f32":
+        return (16 if N <= 96 else 8), 2, (64 if N <= 64 else (128 if N <= 256 else 256))
+    return (8 if N <= 96 else 4), 2, 64
+
+
+def _at(TB, csize, S):
+    rows_per_line = max(128 // (TB * csize), 1)
+
+    def row_of(idx):
+        return idx ^ ((idx // S) & 1) if TB * csize == 64 else idx
+
+    def swz(row):
+        return ((row // rows_per_line) & (TB // 2 - 1)) << 1 if TB >= 4 else 0
+
+    def at(idx, b):
+        row = row_of(idx)
+        return row * TB + (b ^ swz(row))
+    return at
+
+
+def _wavefronts(word_addrs, access_bytes):
+    per = 128 // access_bytes
+    words = access_bytes // 4
+    total = 0
+    for p in range(0, 32, per):
+        banks = defaultdict(set)
+        for a in word_addrs[p:p + per]:
+            if a is None:
+                continue
+            for w in range(words):
+                banks[(a + w) % 32].add(a + w)
+        total += max((len(v) for v in banks.values()), default=0)
+    return total
+
+
+@pytest.mark.parametrize("menu,N,radices", _plans())
+@pytest.mark.parametrize("dtype,csize", [("f32", 8), ("f64", 16)])
+def test_position_map_is_a_bijection(menu, N, radices, dtype, csize):
+    TB, _, _ = _tiles(N, radices, dtype)
+    at = _at(TB, csize, radices[0])
+    pos = sorted(at(i, b) for i in range(N) for b in range(TB))
+    assert pos == list(range(N * TB))
+
+
+@pytest.mark.parametrize("menu,N,radices", _plans())
+def test_fp32_passes_are_bank_conflict_free(menu, N, radices):
+    TB, V, NT = _tiles(N, radices, "f32")
+    at = _at(TB, 8, radices[0])
+    G = TB // V
+    Ns = 1
+    for R in radices:
+        NB = N // R
+        total = NB * G
+        for w in range(NT // 32):
+            for it in range((total + NT - 1) // NT):
+                us = [w * 32 + lane + it * NT for lane in range(32)]
+                active = sum(u < total for u in us)
+                if not active:
+                    continue
+                for r in range(R):
+                    loads, stores = [], []
+                    for u in us:
+                        if u >= total:
+                            loads.append(None)
+                            stores.append(None)
+                            continue
+                        j, b0 = u // G, (u % G) * V
+                        k = j % Ns
+                        loads.append(2 * at(j + r * NB, b0))
+                        stores.append(2 * at((j - k) * R + k + r * Ns, b0))
+                    minimum = (active * 16 + 127) // 128
+                    assert _wavefronts(loads, 16) == minimum, (N, radices, R, "load")
+                    assert _wavefronts(stores, 16) == minimum, (N, radices, R, "store")
+        Ns *= R
+
+
+def test_menus_parsed():
+    rows, cols = _menu("TF_CT_MENU"), _menu("TF_CT_MENU_COLS_F32")
+    assert (224, 8, 4, 7) in rows and (224, 16, 14) in cols
+    assert [e[0] for e in rows] == [e[0] for e in cols]
