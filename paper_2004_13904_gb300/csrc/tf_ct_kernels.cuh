@@ -354,15 +354,22 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
 }
 
 // Dynamic shared memory above 48 KB needs an opt-in; it is raised only when a launch needs
-// more than any earlier launch of the same kernel, so steady-state launches (and launches
-// under CUDA-graph capture) make no attribute call.
+// more than any earlier launch of the same kernel on the current device (the attribute
+// is per device), so steady-state launches (and launches under CUDA-graph capture) make
+// no attribute call.
+constexpr int kSmemDevices = 64;
 template <auto Kernel> inline cudaError_t set_smem(size_t smem) {
-  static std::atomic<size_t> granted{0};   // one per kernel
-  size_t have = granted.load(std::memory_order_relaxed);
+  static std::atomic<size_t> granted[kSmemDevices];   // one per kernel and device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kSmemDevices)
+    return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  size_t have = granted[dev].load(std::memory_order_relaxed);
   if (smem <= have) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    while (have < smem && !granted.compare_exchange_weak(have, smem)) {}
+    while (have < smem && !granted[dev].compare_exchange_weak(have, smem)) {}
   return e;
 }
 

@@ -70,6 +70,11 @@ template <typename T> cudaError_t launch_rows_r2c(const RowsR2C<T>& a, int ncols
 template <typename T> cudaError_t launch_rows_c2r(const RowsC2R<T>& a, int ncols, int tb, cudaStream_t s);
 template <typename T> cudaError_t launch_cols_fwd(const ColsFwd<T>& a, int ncols, int tk, cudaStream_t s);
 template <typename T> cudaError_t launch_cols_adj(const ColsAdj<T>& a, int ncols, int tk, cudaStream_t s);
+// Loads the generic engine's forward-product kernels (rows_r2c, cols_fwd, rows_c2r) on
+// the current device and raises their shared-memory limits for lengths n1 (row
+// transforms, tw1 twiddles) and n2 (column transforms), rows tile tb and column tile tk,
+// so that later launches of that configuration make no load or attribute call.
+template <typename T> cudaError_t prepare_forward_generic(int n1, int tw1, int n2, int tw2, int tb, int tk);
 // Compile-time-plan variants of the four product stages (tf_ct_kernels.cuh); they
 // return cudaErrorNotSupported, before any CUDA call, for lengths off their menu.
 template <typename T> cudaError_t ct_rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s);

@@ -20,6 +20,7 @@ namespace tfk {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kSmemDevices = 64;   // devices with a per-device shared-memory record
 
 template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
 template <> struct Log2<1> { static constexpr int value = 0; };
@@ -387,17 +388,33 @@ __global__ void k_to_f32(const double2* __restrict__ src, float2* __restrict__ d
 }
 
 // Raises a kernel's dynamic shared-memory limit when a launch needs more than any
-// earlier one did, so that steady-state launches (and launches under CUDA-graph
-// capture) make no attribute call.
+// earlier one did on the current device, so that steady-state launches (and launches
+// under CUDA-graph capture) make no attribute call.  The attribute is per device, so the
+// record is too.
 template <auto Kernel>
 cudaError_t prep(size_t smem) {
-  static std::atomic<size_t> granted{0};   // one per kernel
-  size_t have = granted.load(std::memory_order_relaxed);
+  static std::atomic<size_t> granted[kSmemDevices];   // one per kernel and device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kSmemDevices)
+    return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  size_t have = granted[dev].load(std::memory_order_relaxed);
   if (smem <= have) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    while (have < smem && !granted.compare_exchange_weak(have, smem)) {}
+    while (have < smem && !granted[dev].compare_exchange_weak(have, smem)) {}
   return e;
+}
+
+// Loads a kernel's code on the current device now (CUDA loads modules lazily, at a
+// kernel's first launch, which allocates device memory) and raises its shared-memory
+// limit for launches of `smem` bytes.
+template <auto Kernel>
+cudaError_t load_and_prep(size_t smem) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, Kernel);
+  return e == cudaSuccess ? prep<Kernel>(smem) : e;
 }
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
@@ -484,6 +501,37 @@ cudaError_t launch_cols_adj(const ColsAdj<T>& a, int ncols, int tk, cudaStream_t
     default: return cudaErrorInvalidValue;
   }
 }
+
+template <typename T, int TB>
+static cudaError_t prep_rows_tb(int n, int tw_count) {
+  const size_t sm = smem_rows(n, tw_count, TB, sizeof(typename CT<T>::C));
+  cudaError_t e = load_and_prep<k_rows_r2c<T, TB>>(sm);
+  return e == cudaSuccess ? load_and_prep<k_rows_c2r<T, TB>>(sm) : e;
+}
+template <typename T, int TK>
+static cudaError_t prep_cols_fwd_tk(int n, int tw_count) {
+  return load_and_prep<k_cols_fwd<T, TK>>(smem_cols(n, tw_count, TK, sizeof(typename CT<T>::C)));
+}
+
+template <typename T>
+cudaError_t prepare_forward_generic(int n1, int tw1, int n2, int tw2, int tb, int tk) {
+  cudaError_t e;
+  switch (tb) {
+    case 4: e = prep_rows_tb<T, 4>(n1, tw1); break;
+    case 8: e = prep_rows_tb<T, 8>(n1, tw1); break;
+    case 16: e = prep_rows_tb<T, 16>(n1, tw1); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  switch (tk) {
+    case 4: return prep_cols_fwd_tk<T, 4>(n2, tw2);
+    case 8: return prep_cols_fwd_tk<T, 8>(n2, tw2);
+    case 16: return prep_cols_fwd_tk<T, 16>(n2, tw2);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t prepare_forward_generic<float>(int, int, int, int, int, int);
+template cudaError_t prepare_forward_generic<double>(int, int, int, int, int, int);
 
 template cudaError_t launch_rows_r2c<float>(const RowsR2C<float>&, int, int, cudaStream_t);
 template cudaError_t launch_rows_r2c<double>(const RowsR2C<double>&, int, int, cudaStream_t);
