@@ -84,8 +84,9 @@ tf_status tf_create_gravity(const tf_grid* grid, tf_dtype dtype, tf_stream strea
 tf_status tf_create_magnetic(const tf_grid* grid, double inc_deg, double dec_deg,
                              double field_nt, tf_dtype dtype, tf_stream stream, tf_op** out);
 
-/* Release the operator and everything it owns (waits for its work to finish).
- * NULL is accepted. */
+/* Release the operator and everything it owns (waits for the device's work to finish).
+ * NULL is accepted.  Returns TF_ECUDA if that wait reports a fault of earlier work; the
+ * operator is released either way. */
 tf_status tf_destroy(tf_op* op);
 
 /* m = sx*sy, n = nx*ny*nz. */
@@ -116,6 +117,27 @@ tf_status tf_matmat(tf_op* op, int64_t B, const void* X, int64_t ldx, void* D, i
  * (X^T G^T = (G X)^T and Y^T G = (G^T Y)^T need no further entry, App. A.) */
 tf_status tf_rmatmat(tf_op* op, int64_t B, const void* Y, int64_t ldy, void* X, int64_t ldx,
                      const void* colscale, const void* rowscale, tf_stream stream);
+
+/* D = diag(rowscale) G diag(colscale) X for B1 columns and XT = diag(colscale) G^T
+ * diag(rowscale) Y for B2 columns, from and to HOST memory, with the copies inside the
+ * call (App. A, as tf_matmat / tf_rmatmat).  X (ldx >= n), D (ldd >= m), Y (ldy >= m) and
+ * XT (ldxt >= n) are host pointers to column-major blocks; either product may be empty
+ * (B = 0, its pointers may then be NULL); colscale / rowscale are DEVICE vectors or NULL.
+ * The columns go through the device in `chunks` chunks (>= 1): the host-to-device copy of
+ * one chunk, the products of another and the device-to-host copy of a third overlap on two
+ * internal copy streams and the caller's stream, with G^T's chunks ahead of G's so that
+ * the two large copies (X in, XT out) use both directions of the host link at once.
+ * Device staging (three slots per product, each one chunk's input and output) is kept in
+ * the operator and grown on demand (growth frees and allocates device memory).  The call
+ * is stream-ordered: the copies start after the work already queued on `stream`, and
+ * `stream` continues after the last copy out, so the caller synchronises `stream` before
+ * reading D or XT.  Copies overlap only from page-locked host memory.  The host blocks
+ * must not change before that point.  Errors: TF_EINVAL (negative B, chunks < 1, NULL
+ * block of a non-empty product, leading dimension below the rows), TF_ENOMEM, TF_ECUDA. */
+tf_status tf_products_host(tf_op* op, int64_t B1, const void* X, int64_t ldx, void* D,
+                           int64_t ldd, int64_t B2, const void* Y, int64_t ldy, void* XT,
+                           int64_t ldxt, const void* colscale, const void* rowscale, int chunks,
+                           tf_stream stream);
 
 /* Copy the operator's layer spectra, nz x n2 x (n1/2+1) complex values of its dtype
  * (interleaved re/im, k1 fastest), already divided by n1*n2, to dst (device or host
@@ -151,23 +173,28 @@ tf_status tf_get_engine(const tf_op* op, int* engine, int* compiled_rows, int* c
 tf_status tf_profile_enable(tf_op* op, int enable);
 tf_status tf_profile_read(tf_op* op, double* ms, int64_t* launches, int64_t* columns);
 
-/* d = diag(rowscale) G diag(colscale) x for one column, like tf_matvec, but without
- * allocating anything.  The paper has no counterpart: this entry point exists for
+/* d = diag(rowscale) G diag(colscale) x for one column, as tf_matvec computes it, but
+ * without allocating anything.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc when they run the product -- for example code
- * running under a memory budget that forbids new device allocations, or between
- * points where an allocator must not be entered.  The operator itself must have been
- * created beforehand (creation allocates).  Instead of the operator's workspace the
- * call uses a fixed 8 MiB scratch buffer compiled into the library (a __device__ array
- * that every GPU loading the library holds until the process exits).
- *  - The first call on a device looks up the buffer's address there; make that first
- *    call before any stream capture.  The current device must be the operator's.
- *  - All calls share the one buffer, which keeps the previous call's contents (every
- *    value the product reads from it is written first in the same call).  Calls that
+ * running under a memory budget that forbids new device allocations, or between points
+ * where an allocator must not be entered.  The operator itself must have been created
+ * beforehand (creation allocates).  Instead of the operator's workspace the call uses a
+ * fixed 8 MiB scratch buffer compiled into the library (a __device__ array that a device
+ * holds from the creation of the first operator on it until the process exits).
+ *  - Operator creation (tf_create_*) looks up the buffer's address on its device and
+ *    loads the kernels this call launches, so the call itself loads no code and makes no
+ *    allocation, on its first use as on any later one.  The current device must be the
+ *    operator's.
+ *  - The call always runs the generic FFT engine (whatever tf_set_engine selected), so
+ *    its result agrees with tf_matvec's within the product tolerances, not bitwise.
+ *  - All calls share the one buffer, which keeps the previous call's contents; the
+ *    kernels read it only at positions written earlier in the same call.  Calls that
  *    overlap on the GPU -- on different streams, or from different host threads without
  *    ordering -- race on the buffer and give wrong results.
  *  - Errors: TF_EINVAL if the operator needs more than 8 MiB of scratch for one column
- *    (nz*ny*(n1/2+1) + sy*(n1/2+1) complex values of its dtype, plus alignment), if x or
- *    d is NULL, or if another device is current; TF_ECUDA if a launch fails. */
+ *    ((nz*ny + n2)*hs + (sy + n2)*hs complex values of its dtype, hs = n1/2+1 rounded up
+ *    to a multiple of 16, plus alignment), if x or d is NULL, or if another device is
+ *    current; TF_ECUDA if a launch fails. */
 tf_status tf_matvec_noalloc(const tf_op* op, const void* x, void* d, const void* colscale,
                             const void* rowscale, tf_stream stream);
 
@@ -217,8 +244,9 @@ tf_status tf_peak_probe(tf_dtype dtype, double* tflops, tf_stream stream);
  * tf_gkb projects with t_p steps of Golub-Kahan bidiagonalisation of G~ started from r~
  * (Alg. 1) with re-orthogonalisation of both bases (classical Gram-Schmidt applied
  * twice, or modified Gram-Schmidt), UPRE on the t largest singular values of the
- * (t_p+1) x t_p bidiagonal B, and the Tikhonov solution on all t_p terms, i.e. the least
- * squares solution of [B; alpha I] y = [||r~|| e_1; 0] (Givens QR), z = A y.
+ * (t_p+1) x t_p bidiagonal B (from its Golub-Kahan tridiagonal form), and the Tikhonov
+ * solution on all t_p terms, i.e. the least squares solution of
+ * [B; alpha I] y = [||r~|| e_1; 0] (Givens QR), z = A y.
  * tf_rsvd projects with the randomised SVD of Alg. 2 with one power iteration from the
  * caller's Gaussian test matrix Omega, keeps the t largest singular values of B = G~ Q
  * (eigen-decomposition of B^T B) and z = Q V_t Gamma(alpha) U_t^T r~.
@@ -284,8 +312,12 @@ tf_status tf_batch_products(tf_batch* batch, int64_t B, const void* const* X, vo
  * iteration with Wilkinson shifts, together with the first component of each unit
  * eigenvector (the Golub-Welsch weights' square roots, up to sign).  Overwrites d with
  * the eigenvalues (unordered) and writes first[0..n); e is destroyed (needs n entries).
- * The GKB driver applies it to B B^T, whose eigenvalues are s_i^2 and whose eigenvectors'
- * first components are the first row of U (Alg. 1).  Errors: TF_EINVAL, TF_ENOTCONV.
+ * An off-diagonal entry counts as zero below eps times its diagonal neighbours or eps
+ * times the matrix's infinity norm (eigenvalues to absolute accuracy eps ||T||).  The GKB
+ * driver applies it to the Golub-Kahan form of B (zero diagonal, off-diagonal gam_0,
+ * bet_0, gam_1, bet_1, ...), whose positive eigenvalues are the singular values s_i and
+ * whose eigenvectors' first components are the first row of U over sqrt(2) (Alg. 1).
+ * Errors: TF_EINVAL, TF_ENOTCONV.
  *
  * tf_damped_bidiag_solve: y = argmin ||[B; alpha I] y - [b0 e_1; 0]|| for the lower
  * bidiagonal (tp+1) x tp matrix B with diagonal gam[0..tp) and subdiagonal bet[0..tp)

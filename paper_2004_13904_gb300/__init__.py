@@ -169,100 +169,59 @@ class Operator:
                                          self._ptr(rs), self._stream()))
         return out
 
-    # -- host buffers: copies overlapped with the products ------------------------------
-    def _host_pipeline(self, fn, H, rows_out, out_host, chunks):
-        """Run fn (a block product) on a pinned host block H (B x rows_in) in `chunks`
-        column chunks: chunk c's host-to-device copy, product and device-to-host copy run
-        on three streams ordered by events, so copies of one chunk overlap the product of
-        another.  The caller's current stream is ordered after all of it."""
+    # -- host buffers: copies overlapped with the products (tf_products_host) -----------
+    def _host_block(self, t, rows, name):
         torch = _torch()
-        B = H.shape[0]
-        if out_host is None:
-            out_host = torch.empty((B, rows_out), dtype=self.dtype, pin_memory=True)
-        if B == 0:
-            return out_host
-        main = torch.cuda.current_stream(self.device)
-        if not hasattr(self, "_copy_streams"):
-            self._copy_streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
-        s_in, s_out = self._copy_streams
-        din, dout = self._device_bufs(B, H.shape[1], rows_out)
-        n = max(1, min(chunks, B))
-        edges = [B * i // n for i in range(n + 1)]
-        s_in.wait_stream(main)
-        s_out.wait_stream(main)
-        for c in range(n):
-            a, b = edges[c], edges[c + 1]
-            if a == b:
-                continue
-            with torch.cuda.stream(s_in):
-                din[a:b].copy_(H[a:b], non_blocking=True)
-            main.wait_stream(s_in)
-            fn(din[a:b], out=dout[a:b])
-            s_out.wait_stream(main)
-            with torch.cuda.stream(s_out):
-                out_host[a:b].copy_(dout[a:b], non_blocking=True)
-        main.wait_stream(s_out)
-        return out_host
+        if not isinstance(t, torch.Tensor) or t.device.type != "cpu" or t.dtype != self.dtype:
+            raise TypeError(f"{name} must be a {self.dtype} host tensor")
+        if t.dim() == 1:
+            t = t.view(1, -1)
+        if t.dim() != 2 or t.shape[1] != rows or t.stride(1) != 1 or (
+                t.shape[0] > 1 and t.stride(0) < rows):
+            raise ValueError(f"{name} must have shape (B, {rows}) with unit inner stride")
+        return t, (t.stride(0) if t.shape[0] > 1 else rows)
 
-    def _device_bufs(self, B, rows_in, rows_out):
-        """Device staging blocks for host-buffer products, kept per shape."""
+    def products_host(self, X_host=None, Y_host=None, D_host=None, XT_host=None, chunks: int = 8,
+                      colscale=None, rowscale=None):
+        """G X and G^T Y for host blocks X (B1 x n) and Y (B2 x m) into host blocks
+        D (B1 x m) and XT (B2 x n) (allocated pinned when not given); returns (D, XT).
+
+        One tf_products_host call: the columns go through the device in `chunks` chunks
+        whose copies in, products and copies out overlap (G^T's chunks ahead of G's, so
+        that the two large copies use both directions of the host link).  Ordered on the
+        current stream; synchronise it before reading the results.  Pass pinned tensors
+        for overlapped copies."""
         torch = _torch()
-        cache = self.__dict__.setdefault("_host_bufs", {})
-        key = (B, rows_in, rows_out)
-        if key not in cache:
-            cache[key] = (torch.empty((B, rows_in), dtype=self.dtype, device=self.device),
-                          torch.empty((B, rows_out), dtype=self.dtype, device=self.device))
-        return cache[key]
-
-    def products_host(self, X_host, Y_host, D_host=None, XT_host=None, chunks: int = 4):
-        """G X and G^T Y for two independent pinned host blocks X (B1 x n) and Y (B2 x m),
-        into pinned host blocks D (B1 x m) and XT (B2 x n); returns (D, XT).
-
-        Both products run as one pipeline of `chunks` column chunks: per chunk, Y's copy
-        in, the G^T product and the copy out of its result, then the same for X and G.  The
-        large copies of the two directions (X in, G^T Y out) then overlap on the
-        full-duplex host link instead of following each other.  The caller's current
-        stream is ordered after all of it."""
-        torch = _torch()
-        B1, B2 = X_host.shape[0], Y_host.shape[0]
+        if X_host is None:
+            X_host = torch.empty((0, self.n), dtype=self.dtype)
+        if Y_host is None:
+            Y_host = torch.empty((0, self.m), dtype=self.dtype)
+        X, ldx = self._host_block(X_host, self.n, "X")
+        Y, ldy = self._host_block(Y_host, self.m, "Y")
+        B1, B2 = X.shape[0], Y.shape[0]
         if D_host is None:
-            D_host = torch.empty((B1, self.m), dtype=self.dtype, pin_memory=True)
+            D_host = torch.empty((B1, self.m), dtype=self.dtype, pin_memory=B1 > 0)
         if XT_host is None:
-            XT_host = torch.empty((B2, self.n), dtype=self.dtype, pin_memory=True)
-        main = torch.cuda.current_stream(self.device)
-        if not hasattr(self, "_copy_streams"):
-            self._copy_streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
-        s_in, s_out = self._copy_streams
-        xin, dout = self._device_bufs(B1, self.n, self.m)
-        yin, xtout = self._device_bufs(B2, self.m, self.n)
-        n = max(1, chunks)
-        ex = [B1 * i // n for i in range(n + 1)]
-        ey = [B2 * i // n for i in range(n + 1)]
-        s_in.wait_stream(main)
-        s_out.wait_stream(main)
-        for c in range(n):
-            for (H, din, dres, R, e, fn) in ((Y_host, yin, xtout, XT_host, ey, self.rmatmat),
-                                             (X_host, xin, dout, D_host, ex, self.matmat)):
-                a, b = e[c], e[c + 1]
-                if a == b:
-                    continue
-                with torch.cuda.stream(s_in):
-                    din[a:b].copy_(H[a:b], non_blocking=True)
-                main.wait_stream(s_in)
-                fn(din[a:b], out=dres[a:b])
-                s_out.wait_stream(main)
-                with torch.cuda.stream(s_out):
-                    R[a:b].copy_(dres[a:b], non_blocking=True)
-        main.wait_stream(s_out)
+            XT_host = torch.empty((B2, self.n), dtype=self.dtype, pin_memory=B2 > 0)
+        D, ldd = self._host_block(D_host, self.m, "D")
+        XT, ldxt = self._host_block(XT_host, self.n, "XT")
+        if D.shape[0] != B1 or XT.shape[0] != B2:
+            raise ValueError("output blocks must have as many columns as the inputs")
+        cs = self._vec(colscale, self.n, "colscale")
+        rs = self._vec(rowscale, self.m, "rowscale")
+        p = lambda t: ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+        _lib.check(_lib.lib().tf_products_host(
+            self._h, B1, p(X), ldx, p(D), ldd, B2, p(Y), ldy, p(XT), ldxt, self._ptr(cs),
+            self._ptr(rs), int(chunks), self._stream()))
         return D_host, XT_host
 
     def matmat_host(self, X_host, out_host=None, chunks: int = 4):
-        """G X for a pinned host block X (B x n) into pinned host memory (B x m)."""
-        return self._host_pipeline(self.matmat, X_host, self.m, out_host, chunks)
+        """G X for a host block X (B x n) into host memory (B x m)."""
+        return self.products_host(X_host, None, out_host, None, chunks)[0]
 
     def rmatmat_host(self, Y_host, out_host=None, chunks: int = 4):
-        """G^T Y for a pinned host block Y (B x m) into pinned host memory (B x n)."""
-        return self._host_pipeline(self.rmatmat, Y_host, self.n, out_host, chunks)
+        """G^T Y for a host block Y (B x m) into host memory (B x n)."""
+        return self.products_host(None, Y_host, None, out_host, chunks)[1]
 
     # -- introspection ------------------------------------------------------------------
     def spectra(self):

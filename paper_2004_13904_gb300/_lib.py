@@ -66,6 +66,7 @@ SIGNATURES = {
     "tf_matmat": [vp, i64, vp, i64, vp, i64, vp, vp, vp],
     "tf_rmatmat": [vp, i64, vp, i64, vp, i64, vp, vp, vp],
     "tf_get_spectra": [vp, vp, i64, vp],
+    "tf_products_host": [vp, i64, vp, i64, vp, i64, i64, vp, i64, vp, i64, vp, vp, c_int, vp],
     "tf_set_tuning": [vp, c_int, c_int, i64],
     "tf_get_tuning": [vp, P(c_int), P(c_int), P(i64)],
     "tf_profile_enable": [vp, c_int],

@@ -181,6 +181,13 @@ struct tf_op {
   int rows_tile = 8, cols_tile = 8;
   bool ct1 = false, ct2 = false;  // compile-time plans exist for n1 / n2
   int engine = 0;                 // 0: compile-time plans where available, 1: generic
+  // host-buffer pipeline (tf_products_host): device staging slots and their streams/events
+  static constexpr int kSlots = 3;
+  void* stage[2][kSlots] = {};   // [direction][slot]: one chunk's input then output
+  size_t stage_bytes = 0;        // bytes of each slot
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2][kSlots] = {}, ev_cmp[2][kSlots] = {}, ev_out[2][kSlots] = {};
+  cudaEvent_t ev_fork = nullptr;
   // profiling
   bool prof = false;
   struct Rec { int stage; int64_t cols; cudaEvent_t a, b; };
@@ -205,9 +212,80 @@ void free_op(tf_op* op) {
   cudaFree(op->spec);
   cudaFree(op->w1);
   cudaFree(op->w2);
+  for (int dir = 0; dir < 2; ++dir)
+    for (int k = 0; k < tf_op::kSlots; ++k) {
+      cudaFree(op->stage[dir][k]);
+      if (op->ev_in[dir][k]) cudaEventDestroy(op->ev_in[dir][k]);
+      if (op->ev_cmp[dir][k]) cudaEventDestroy(op->ev_cmp[dir][k]);
+      if (op->ev_out[dir][k]) cudaEventDestroy(op->ev_out[dir][k]);
+    }
+  if (op->ev_fork) cudaEventDestroy(op->ev_fork);
+  if (op->s_in) cudaStreamDestroy(op->s_in);
+  if (op->s_out) cudaStreamDestroy(op->s_out);
   for (auto& r : op->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : op->pool) cudaEventDestroy(e);
   delete op;
+}
+
+// ---- scratch of the allocation-free forward product (tf_matvec_noalloc) ---------------
+//
+// A file-scope __device__ array: every device on which the library's module is loaded
+// holds kNoallocScratchBytes of it until the process exits.  Host code cannot use the
+// array's name as a device address; the address is looked up per device with
+// cudaGetSymbolAddress.  That lookup loads this module under CUDA's lazy loading (an
+// allocation), so it is made when an operator is created (tf_create_*), never by
+// tf_matvec_noalloc itself.
+
+constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Scratch layout for one column: the row-transformed layers (W1) at 0 and the column-stage
+// output (W2) at noalloc_w2_offset, each followed by the same guard tail of n2*hs values
+// that the operator's own workspace buffers carry.
+size_t noalloc_guard(const tf_op* op) { return (size_t)op->n2 * op->hs * op->csize(); }
+size_t noalloc_w2_offset(const tf_op* op) {
+  return round256((size_t)op->w1_per_col() * op->csize() + noalloc_guard(op));
+}
+size_t noalloc_need(const tf_op* op) {
+  return noalloc_w2_offset(op) + (size_t)op->w2_per_col() * op->csize() + noalloc_guard(op);
+}
+
+// Address of the scratch array on device dev (looked up once, then cached).
+cudaError_t noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+// Everything tf_matvec_noalloc would otherwise do on its first call on the operator's
+// device: look up the scratch address (which loads the module holding it) and load the
+// generic forward kernels at the operator's tiles with their shared-memory limits raised.
+// Runs at creation and whenever the tiles change; a no-op for operators too large for the
+// scratch.  The operator's device must be current.
+tf_status noalloc_prepare(const tf_op* op) {
+  if (noalloc_need(op) > kNoallocScratchBytes) return TF_OK;
+  void* p = nullptr;
+  cudaError_t e = noalloc_scratch(op->device, &p);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+  e = op->dtype == TF_F32
+          ? tfk::prepare_forward_generic<float>(op->n1, op->p1.plan.tw_count, op->n2,
+                                                op->p2.plan.tw_count, op->rows_tile, op->cols_tile)
+          : tfk::prepare_forward_generic<double>(op->n1, op->p1.plan.tw_count, op->n2,
+                                                 op->p2.plan.tw_count, op->rows_tile, op->cols_tile);
+  return e == cudaSuccess ? TF_OK : cuda_fail(e, "loading the generic product kernels");
 }
 
 tf_status upload_twiddles(const HostPlan& h, tf_dtype dt, void** dst) {
@@ -393,6 +471,7 @@ tf_status create_common(const tf_grid* g, int kind, double inc, double dec, doub
   TF_TRY(cudaStreamSynchronize(s), "spectra set-up");
   op->chunk_cap = default_chunk_cap(op);
   if ((st = alloc_workspace(op, 1)) != TF_OK) goto done;
+  if ((st = noalloc_prepare(op)) != TF_OK) goto done;
 
 done:
 #undef TF_TRY
@@ -545,9 +624,11 @@ tf_status tf_create_magnetic(const tf_grid* grid, double inc_deg, double dec_deg
 
 tf_status tf_destroy(tf_op* op) {
   if (!op) return TF_OK;
-  cudaDeviceSynchronize();
+  // A fault of earlier work surfaces here; report it rather than let the next call on
+  // this device be the first to see it.
+  const cudaError_t e = cudaDeviceSynchronize();
   free_op(op);
-  return TF_OK;
+  return e == cudaSuccess ? TF_OK : cuda_fail(e, "work pending at tf_destroy");
 }
 
 tf_status tf_dims(const tf_op* op, int64_t* m, int64_t* n) {
@@ -610,6 +691,117 @@ tf_status tf_rmatvec(tf_op* op, const void* y, void* x, const void* colscale,
   return tf_rmatmat(op, 1, y, op->m(), x, op->n(), colscale, rowscale, stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Streams, events and staging slots of the host-buffer pipeline, created on first use and
+// grown when a call needs larger slots (growth frees and allocates, which waits for the
+// device to be idle).
+tf_status ensure_host_pipeline(tf_op* op, size_t slot_bytes) {
+  cudaError_t e = cudaSuccess;
+  if (!op->s_in) {
+    if ((e = cudaStreamCreateWithFlags(&op->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&op->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "host pipeline streams");
+    for (int dir = 0; dir < 2; ++dir)
+      for (int k = 0; k < tf_op::kSlots; ++k)
+        if ((e = cudaEventCreateWithFlags(&op->ev_in[dir][k], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&op->ev_cmp[dir][k], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&op->ev_out[dir][k], cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_fail(e, "host pipeline events");
+  }
+  if (op->stage_bytes >= slot_bytes) return TF_OK;
+  for (int dir = 0; dir < 2; ++dir)
+    for (int k = 0; k < tf_op::kSlots; ++k) {
+      cudaFree(op->stage[dir][k]);
+      op->stage[dir][k] = nullptr;
+    }
+  op->stage_bytes = 0;
+  for (int dir = 0; dir < 2; ++dir)
+    for (int k = 0; k < tf_op::kSlots; ++k)
+      if ((e = cudaMalloc(&op->stage[dir][k], slot_bytes)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(host pipeline staging)");
+  op->stage_bytes = slot_bytes;
+  return TF_OK;
+}
+
+// cb columns of `rows` values between a column-major block (leading dimension ld, in
+// elements) and a packed one, as one copy when the columns are contiguous.
+cudaError_t copy_cols(void* dst, int64_t dld, const void* src, int64_t sld, int64_t rows,
+                      int64_t cb, size_t esz, cudaMemcpyKind kind, cudaStream_t s) {
+  if (dld == rows && sld == rows)
+    return cudaMemcpyAsync(dst, src, (size_t)(rows * cb) * esz, kind, s);
+  return cudaMemcpy2DAsync(dst, (size_t)dld * esz, src, (size_t)sld * esz, (size_t)rows * esz,
+                           (size_t)cb, kind, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+tf_status tf_products_host(tf_op* op, int64_t B1, const void* X, int64_t ldx, void* D,
+                           int64_t ldd, int64_t B2, const void* Y, int64_t ldy, void* XT,
+                           int64_t ldxt, const void* colscale, const void* rowscale, int chunks,
+                           tf_stream stream) {
+  if (check_op(op)) return TF_EINVAL;
+  if (B1 < 0 || B2 < 0 || chunks < 1) return fail(TF_EINVAL, "need B1, B2 >= 0 and chunks >= 1");
+  if ((B1 > 0 && (!X || !D || ldx < op->n() || ldd < op->m())) ||
+      (B2 > 0 && (!Y || !XT || ldy < op->m() || ldxt < op->n())))
+    return fail(TF_EINVAL, "null block or leading dimension below the block's rows");
+  if (B1 == 0 && B2 == 0) return TF_OK;
+  const size_t esz = op->dtype == TF_F32 ? sizeof(float) : sizeof(double);
+  const int64_t cmax = (std::max(B1, B2) + chunks - 1) / chunks;   // columns per chunk
+  const size_t slot = (size_t)cmax * (size_t)(op->n() + op->m()) * esz;
+  tf_status st = ensure_host_pipeline(op, slot);
+  if (st != TF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+#define TF_HP(call, what) \
+  do { if ((e = (call)) != cudaSuccess) return cuda_fail(e, what); } while (0)
+  // the copy streams start after everything already queued on the caller's stream
+  TF_HP(cudaEventRecord(op->ev_fork, s), "cudaEventRecord");
+  TF_HP(cudaStreamWaitEvent(op->s_in, op->ev_fork, 0), "cudaStreamWaitEvent");
+  TF_HP(cudaStreamWaitEvent(op->s_out, op->ev_fork, 0), "cudaStreamWaitEvent");
+  // Per chunk: G^T's columns first, then G's, so that the two large copies (X in, G^T Y
+  // out) of neighbouring chunks overlap on the full-duplex host link.  Chunk c of a
+  // direction uses slot c % kSlots once the copy out of the slot's previous chunk is done.
+  int64_t chunk_no[2] = {0, 0};
+  for (int c = 0; c < chunks; ++c) {
+    for (int dir = 1; dir >= 0; --dir) {
+      const int64_t Bd = dir ? B2 : B1;
+      const int64_t c0 = Bd * c / chunks, c1 = Bd * (c + 1) / chunks, cb = c1 - c0;
+      if (cb <= 0) continue;
+      const int k = (int)(chunk_no[dir]++ % tf_op::kSlots);
+      const int64_t rin = dir ? op->m() : op->n(), rout = dir ? op->n() : op->m();
+      unsigned char* din = (unsigned char*)op->stage[dir][k];
+      unsigned char* dout = din + (size_t)cb * rin * esz;
+      const unsigned char* hin = (const unsigned char*)(dir ? Y : X) + (size_t)(c0 * (dir ? ldy : ldx)) * esz;
+      unsigned char* hout = (unsigned char*)(dir ? XT : D) + (size_t)(c0 * (dir ? ldxt : ldd)) * esz;
+      TF_HP(cudaStreamWaitEvent(op->s_in, op->ev_out[dir][k], 0), "cudaStreamWaitEvent");
+      TF_HP(copy_cols(din, rin, hin, dir ? ldy : ldx, rin, cb, esz, cudaMemcpyHostToDevice, op->s_in),
+            "host-to-device copy");
+      TF_HP(cudaEventRecord(op->ev_in[dir][k], op->s_in), "cudaEventRecord");
+      TF_HP(cudaStreamWaitEvent(s, op->ev_in[dir][k], 0), "cudaStreamWaitEvent");
+      st = dir ? tf_rmatmat(op, cb, din, rin, dout, rout, colscale, rowscale, stream)
+               : tf_matmat(op, cb, din, rin, dout, rout, colscale, rowscale, stream);
+      if (st != TF_OK) return st;
+      TF_HP(cudaEventRecord(op->ev_cmp[dir][k], s), "cudaEventRecord");
+      TF_HP(cudaStreamWaitEvent(op->s_out, op->ev_cmp[dir][k], 0), "cudaStreamWaitEvent");
+      TF_HP(copy_cols(hout, dir ? ldxt : ldd, dout, rout, rout, cb, esz, cudaMemcpyDeviceToHost,
+                      op->s_out),
+            "device-to-host copy");
+      TF_HP(cudaEventRecord(op->ev_out[dir][k], op->s_out), "cudaEventRecord");
+    }
+  }
+  // the caller's stream resumes once the last copy out is done
+  TF_HP(cudaEventRecord(op->ev_fork, op->s_out), "cudaEventRecord");
+  TF_HP(cudaStreamWaitEvent(s, op->ev_fork, 0), "cudaStreamWaitEvent");
+#undef TF_HP
+  return TF_OK;
+}
+
 tf_status tf_get_spectra(const tf_op* op, void* dst, int64_t bytes, tf_stream stream) {
   if (check_op(op)) return TF_EINVAL;
   const int64_t need = (int64_t)op->nz * op->n2 * op->nh * (int64_t)op->csize();
@@ -633,8 +825,13 @@ tf_status tf_set_tuning(tf_op* op, int rows_tile, int cols_tile, int64_t chunk_c
   if (tfk::smem_rows(op->n1, op->p1.plan.tw_count, rt, op->csize()) > lim ||
       tfk::smem_cols(op->n2, op->p2.plan.tw_count, ct, op->csize()) > lim)
     return fail(TF_EUNSUPPORTED, "tile needs more than 227 KB of shared memory");
+  const bool retiled = rt != op->rows_tile || ct != op->cols_tile;
   op->rows_tile = rt;
   op->cols_tile = ct;
+  if (retiled) {
+    const tf_status pst = noalloc_prepare(op);
+    if (pst != TF_OK) return pst;
+  }
   if (chunk_cols) {
     op->chunk_cap = chunk_cols;
     if (chunk_cols != op->chunk) {
@@ -789,31 +986,20 @@ tf_status api_fail(tf_status st, const char* fmt, ...) {
 
 // ---- forward product without any allocation --------------------------------------------
 //
-// tf_matvec_noalloc runs the same three product stages as tf_matvec for one column, but
-// takes its scratch (the row-transformed layers and the column-stage output) from a
-// fixed buffer compiled into this library instead of the operator's workspace.  The
-// buffer is a file-scope __device__ array, so every GPU that loads the library holds
-// kNoallocScratchBytes of it until the process exits.  Host code cannot use the array's
-// name as a device address; its address is looked up once per device with
-// cudaGetSymbolAddress (on the first call on that device) and cached.
+// tf_matvec_noalloc runs the generic engine's three forward stages for one column with
+// its scratch (the row-transformed layers and the column-stage output) in the library's
+// fixed device array instead of the operator's workspace.  The generic kernels load the
+// scratch only at positions the same call has written (masked loads of rows < ny,
+// values < nh), so what an earlier call left there never reaches the result.
 
 namespace {
-
-constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;  // 8 MiB
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
-
-constexpr int kNoallocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kNoallocMaxDevices] = {};
-
-size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 template <typename T>
 tf_status noalloc_forward(const tf_op* op, const T* x, T* d, const T* cs, const T* rs,
                           void* scratch, cudaStream_t s) {
   typedef typename CT<T>::C C;
   C* w1 = (C*)scratch;
-  C* w2 = (C*)((unsigned char*)scratch + round256(op->w1_per_col() * op->csize()));
+  C* w2 = (C*)((unsigned char*)scratch + noalloc_w2_offset(op));
   const C* tw1 = (const C*)op->tw1;
   const C* tw2 = (const C*)op->tw2;
   tfk::RowsR2C<T> a;
@@ -844,7 +1030,7 @@ extern "C" tf_status tf_matvec_noalloc(const tf_op* op, const void* x, void* d,
                                        tf_stream stream) {
   if (check_op(op)) return TF_EINVAL;
   if (!x || !d) return fail(TF_EINVAL, "x and d must be non-NULL");
-  const size_t need = round256(op->w1_per_col() * op->csize()) + op->w2_per_col() * op->csize();
+  const size_t need = noalloc_need(op);
   if (need > kNoallocScratchBytes)
     return fail(TF_EINVAL,
                 "tf_matvec_noalloc: this operator needs %zu bytes of scratch per column, more "
@@ -855,19 +1041,9 @@ extern "C" tf_status tf_matvec_noalloc(const tf_op* op, const void* x, void* d,
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev != op->device)
     return fail(TF_EINVAL, "current device %d is not the operator's device %d", dev, op->device);
-  if (dev < 0 || dev >= kNoallocMaxDevices)
-    return fail(TF_EUNSUPPORTED, "device index %d above %d", dev, kNoallocMaxDevices - 1);
   void* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-      g_noalloc_ptr[dev] = p;
-    }
-    scratch = g_noalloc_ptr[dev];
-  }
+  e = noalloc_scratch(dev, &scratch);   // cached since the operator's creation
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
   cudaStream_t s = (cudaStream_t)stream;
   if (op->dtype == TF_F32)
     return noalloc_forward<float>(op, (const float*)x, (float*)d, (const float*)colscale,
