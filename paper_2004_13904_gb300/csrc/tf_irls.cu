@@ -6,9 +6,10 @@
 // its norms on the device (no host round trip per step); the re-orthogonalisation runs in
 // the FP64 / double-float row kernels (tf_rows_dot, tf_rows_axpy).  The projected
 // problems are small and solved on the host in FP64:
-//  * GKB: B B^T is tridiagonal; its eigenvalues are s_i^2 and its eigenvectors' first
-//    components are the first row of U, which is all that UPRE and Eq. (11) use; the
-//    Tikhonov solution on all t_p terms is the least squares solution of
+//  * GKB: the Golub-Kahan form of B (zero diagonal, off-diagonal gam_0, bet_0, gam_1, ...)
+//    is tridiagonal; its positive eigenvalues are the s_i and its eigenvectors' first
+//    components are the first row of U over sqrt(2), which is all that UPRE and Eq. (11)
+//    use; the Tikhonov solution on all t_p terms is the least squares solution of
 //    [B; alpha I] y = [||r~|| e_1; 0], computed with Givens rotations.
 //  * RSVD: QR factors from cuSOLVER, B^T B with cuBLAS, its eigen-decomposition with
 //    cuSOLVER, then the truncated Tikhonov filter on the t largest singular values.
@@ -34,16 +35,24 @@ using tfk::api_fail;
 
 // Implicit QL with Wilkinson shifts on the symmetric tridiagonal (d, e), accumulating
 // only the first row of the eigenvector matrix.  Returns false without convergence.
+// An off-diagonal entry is negligible below eps times its diagonal neighbours, or below
+// eps times the matrix norm (absolute accuracy eps ||T||, the accuracy the iteration has
+// anyway; without it a zero eigenvalue between zero diagonal entries deflates only once
+// its coupling underflows).
 bool tridiag_ql_first(int n, double* d, double* e, double* first) {
   for (int i = 0; i < n; ++i) first[i] = i == 0 ? 1.0 : 0.0;
   if (n <= 1) return true;
   e[n - 1] = 0.0;
+  double tnorm = 0.0;
+  for (int i = 0; i < n; ++i)
+    tnorm = std::max(tnorm, fabs(d[i]) + fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0));
+  const double tiny = DBL_EPSILON * tnorm;
   for (int l = 0; l < n; ++l) {
     for (int iter = 0;; ++iter) {
       int m = l;
       for (; m < n - 1; ++m) {
         const double scale = fabs(d[m]) + fabs(d[m + 1]);
-        if (fabs(e[m]) <= DBL_EPSILON * scale) break;
+        if (fabs(e[m]) <= DBL_EPSILON * scale || fabs(e[m]) <= tiny) break;
       }
       if (m == l) break;
       if (iter >= 64) return false;
@@ -421,7 +430,7 @@ tf_status gkb_run(tf_op* op, const tf_irls_params* p, const void* d_obs, const v
   TRY_CUDA(st.mem.get(&sub, tp), "cudaMalloc(driver)");
   TRY_CUDA(st.mem.get(&coef, std::max(tp + 1, 1)), "cudaMalloc(driver)");
   double* rnorm = st.scal;
-  std::vector<double> gam(tp), bet(tp), dd(tp + 1), ee(tp + 1), first(tp + 1), y(tp);
+  std::vector<double> gam(tp), bet(tp), dd(2 * tp + 1), ee(2 * tp + 1), first(2 * tp + 1), y(tp);
   for (int k = 1; k <= p->kmax; ++k) {
     const double t0 = now_s();
     TRY_TF(st.begin(k));
@@ -450,21 +459,26 @@ tf_status gkb_run(tf_op* op, const tf_irls_params* p, const void* d_obs, const v
     TRY_CUDA(cudaMemcpyAsync(bet.data(), sub, tp * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
     TRY_CUDA(cudaMemcpyAsync(&rn, rnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
     TRY_CUDA(cudaStreamSynchronize(s), "GKB factorisation");
-    // B B^T: diagonal gam_0^2, bet_{i-1}^2 + gam_i^2, bet_{tp-1}^2; off-diagonal gam_i bet_i
-    for (int i = 0; i <= tp; ++i) {
-      const double gi = i < tp ? gam[i] : 0.0, bi = i > 0 ? bet[i - 1] : 0.0;
-      dd[i] = gi * gi + bi * bi;
-      ee[i] = i < tp ? gam[i] * bet[i] : 0.0;
+    // Golub-Kahan form of B: the (2 t_p + 1)-square symmetric tridiagonal matrix with zero
+    // diagonal and off-diagonal gam_0, bet_0, gam_1, bet_1, ... (the matrix [0 B; B^T 0]
+    // with rows and columns interleaved u_1, v_1, u_2, ...).  Its eigenvalues are +-s_i and
+    // 0, and the eigenvector of +s_i is (u_i, v_i) / sqrt(2) interleaved, so its first
+    // component is U(1, i) / sqrt(2).  Working on it instead of on B B^T keeps small s_i
+    // to absolute accuracy eps s_1 rather than eps s_1^2 / s_i.
+    const int ng = 2 * tp + 1;
+    for (int i = 0; i < ng; ++i) {
+      dd[i] = 0.0;
+      ee[i] = i + 1 < ng ? ((i & 1) ? bet[i / 2] : gam[i / 2]) : 0.0;
     }
-    if (!tridiag_ql_first(tp + 1, dd.data(), ee.data(), first.data()))
+    if (!tridiag_ql_first(ng, dd.data(), ee.data(), first.data()))
       return api_fail(TF_ENOTCONV, "tf_gkb: tridiagonal eigenvalue iteration did not converge");
-    std::vector<int> order(tp + 1);
+    std::vector<int> order(ng);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dd[a] > dd[b]; });
     std::vector<double> sv(tp), c2(tp);
-    for (int i = 0; i < tp; ++i) {  // the t_p nonzero eigenvalues are s_i^2
-      sv[i] = sqrt(std::max(dd[order[i]], 0.0));
-      c2[i] = rn * rn * first[order[i]] * first[order[i]];
+    for (int i = 0; i < tp; ++i) {  // the t_p largest eigenvalues are s_1 >= ... >= s_tp
+      sv[i] = std::max(dd[order[i]], 0.0);
+      c2[i] = 2.0 * rn * rn * first[order[i]] * first[order[i]];
     }
     double alpha;
     if (p->alphas) alpha = p->alphas[k - 1];

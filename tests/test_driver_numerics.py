@@ -89,3 +89,39 @@ def test_helpers_reject_bad_arguments():
     L = _lib.lib()
     assert L.tf_damped_bidiag_solve(0, None, None, 1.0, 1.0, None) == _lib.TF_EINVAL
     assert L.tf_tridiag_eig_first(-1, None, None, None) == _lib.TF_EINVAL
+
+
+def test_golub_kahan_route_keeps_small_singular_values():
+    """The GKB driver's projected SVD: the Golub-Kahan tridiagonal of a realistic bidiagonal
+    B (t_p = 1000, singular values graded over ten decades) gives every s_i to absolute
+    accuracy ~eps s_1 and the first row of U to ~eps, against numpy's dense SVD.  The
+    squared route through B B^T would lose the small s_i (error ~eps s_1^2 / s_i)."""
+    rng = np.random.default_rng(17)
+    tp = 1000
+    grade = np.logspace(0, -10, tp)
+    gam = rng.uniform(0.5, 1.5, tp) * grade
+    bet = rng.uniform(0.5, 1.5, tp) * grade
+    B = np.zeros((tp + 1, tp))
+    B[np.arange(tp), np.arange(tp)] = gam
+    B[np.arange(tp) + 1, np.arange(tp)] = bet
+    U, s_ref, _ = np.linalg.svd(B, full_matrices=False)
+    n = 2 * tp + 1
+    e = np.zeros(n - 1)
+    e[0::2] = gam
+    e[1::2] = bet
+    lam, first = tridiag(np.zeros(n), e)
+    order = np.argsort(-lam)[:tp]
+    s = lam[order]
+    assert np.max(np.abs(s - s_ref)) <= 1e-13 * s_ref[0]
+    # U(1, i)^2 = 2 first_i^2 where the singular values are well separated
+    sep = np.r_[np.inf, np.diff(-s_ref)] > 1e-8 * s_ref[0]
+    sep &= np.r_[np.diff(-s_ref), np.inf] > 1e-8 * s_ref[0]
+    assert np.allclose(2 * first[order][sep] ** 2, U[0, sep] ** 2, atol=1e-12)
+    # the B B^T route loses the small values to squaring
+    dd = np.array([(gam[i] if i < tp else 0) ** 2 + (bet[i - 1] if i > 0 else 0) ** 2
+                   for i in range(tp + 1)])
+    lam2, _ = tridiag(dd, gam * bet)
+    s2 = np.sqrt(np.maximum(np.sort(lam2)[::-1][:tp], 0))
+    small = s_ref < 1e-6 * s_ref[0]
+    assert np.max(np.abs(s2 - s_ref)[small] / s_ref[small]) > 1e-3
+    assert np.max(np.abs(s - s_ref)[small] / s_ref[small]) < 1e-3
