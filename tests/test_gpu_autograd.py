@@ -43,40 +43,109 @@ def test_misfit_gradient_matches_dense(dtn):
         assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
 
 
+TOL = {"f64": 1e-12, "f32": 2e-5}      # relative 2-norm tolerance of one product column
+
+
+def _fd_check(f_dir, grad, grad_ref, V, h, eps):
+    """Central differences of the quadratic misfit along each unit direction v, against
+    the back-propagated gradient.  For a quadratic the central difference has no
+    truncation error, so |fd - grad.v| is bounded by rounding alone:
+      * each misfit value 0.5 ||r||^2 is computed from a residual r whose product part is
+        within eps * P of exact (P = ||W_d G x||, the product tolerance per column), so
+        it is off by at most eps ||r|| P + (eps P)^2 / 2, and the difference quotient by
+        (e+ + e-) / (2 h);
+      * grad.v differs from the exact directional derivative by at most
+        ||grad - grad_ref|| (||v|| = 1), grad_ref being the FP64 oracle's gradient.
+    Every direction must meet its own bound (worst case, not a median)."""
+    worst, bounds, derivs = 0.0, 0.0, 0.0
+    for v in V:
+        (fp, rp, pp), (fm, rm, pm) = f_dir(v, h), f_dir(v, -h)
+        fd = (fp - fm) / (2 * h)
+        an = float(grad @ v)
+        e_f = lambda r, p: eps * r * p + 0.5 * (eps * p) ** 2
+        bound = (e_f(rp, pp) + e_f(rm, pm)) / (2 * h) + float(np.linalg.norm(grad - grad_ref))
+        bound *= 1.0 + 1e-9
+        worst = max(worst, abs(fd - an) / bound)
+        bounds += bound
+        derivs += abs(float(grad_ref @ v))
+    assert worst <= 1.0, worst
+    # the bounds are small against the derivatives themselves, so the check pins the
+    # adjoint (a wrong transpose is off by about the derivative's own size)
+    assert bounds < 0.1 * derivs, (bounds, derivs)
+    return worst
+
+
 @pytest.mark.parametrize("dtn", ["f64", "f32"])
 def test_finite_difference_directions_c3(dtn):
-    """Directional derivatives of the weighted misfit on 64 random directions at the
-    c3 magnetic size (150x150 stations, 150x150x20 cells)."""
+    """Directional derivatives of the weighted misfit 0.5 ||W_d (G m - d)||^2 on 64 random
+    unit directions at the c3 magnetic size (150x150 stations, 150x150x20 cells), each
+    within a worst-case rounding bound derived from the product tolerance and h; the
+    back-propagated gradient itself against the FP64 oracle's G^T W_d^2 (G m - d)."""
     import torch
     from paper_2004_13904_gb300.autograd import g_matmat
     dt = torch.float64 if dtn == "f64" else torch.float32
     g = synth.config_grid("c3")
+    T = oop.layer_tables(g, "magnetic", 50.0, 10.0)
     op = _setup(g, "magnetic", 50.0, 10.0, dt)
-    gen = torch.Generator(device="cuda").manual_seed(3)
-    m = (0.1 * torch.rand(g.n, generator=gen, device="cuda", dtype=torch.float64)).to(dt)
-    d = g_matmat(op, (0.1 * torch.rand(g.n, generator=gen, device="cuda",
-                                       dtype=torch.float64)).to(dt)).detach()
-    wd = 1.0 / (0.01 * d.abs() + 0.001 * d.abs().max())
+    rng = np.random.default_rng(3)
+    m = 0.1 * rng.random(g.n)
+    d = oop.fft_matvec(g, T, 0.1 * rng.random(g.n))
+    wd = 1.0 / (0.01 * np.abs(d) + 0.001 * np.abs(d).max())
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    wdt, dwt = t(wd), t(wd * d)
 
-    def f(x):
-        r = wd * (g_matmat(op, x) - d)
-        return 0.5 * (r.double() * r.double()).sum()
+    x = t(m).requires_grad_(True)
+    r = g_matmat(op, x, rowscale=wdt) - dwt
+    (0.5 * (r.double() * r.double()).sum()).backward()
+    grad = x.grad.double().cpu().numpy()
+    grad_ref = oop.fft_rmatvec(g, T, wd * wd * (oop.fft_matvec(g, T, m) - d))
+    assert np.linalg.norm(grad - grad_ref) <= 4 * TOL[dtn] * np.linalg.norm(grad_ref)
 
-    x = m.clone().requires_grad_(True)
-    f(x).backward()
-    grad = x.grad.double()
-    V = torch.randn(64, g.n, generator=gen, device="cuda", dtype=torch.float64)
-    V /= V.norm(dim=1, keepdim=True)
-    h = 1e-3 if dtn == "f64" else 3e-2
-    errs = []
-    with torch.no_grad():
-        for v in V:
-            # the misfit is quadratic, so the central difference is exact up to rounding
-            fd = (f(m + (h * v).to(dt)) - f(m - (h * v).to(dt))) / (2 * h)
-            an = (grad * v).sum()
-            errs.append(float(abs(fd - an) / (abs(an) + 1e-30 * grad.norm())))
-    errs = np.array(errs)
-    assert np.median(errs) < (1e-9 if dtn == "f64" else 2e-2), np.median(errs)
+    def f_dir(v, h):
+        with torch.no_grad():
+            xp = m + h * v
+            gx = g_matmat(op, t(xp), rowscale=wdt)
+            rr = (gx - dwt).double()
+            return (0.5 * float((rr * rr).sum()), float(rr.norm()), float(gx.double().norm()))
+
+    V = rng.standard_normal((64, g.n))
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    worst = _fd_check(f_dir, grad, grad_ref, V, 10.0, TOL[dtn])
+    print(f"c3 {dtn}: worst |fd - grad.v| / bound over 64 directions = {worst:.3f}")
+
+
+@pytest.mark.parametrize("dtn", ["f64", "f32"])
+def test_finite_difference_directions_dense(dtn):
+    """The same worst-case finite-difference check on a grid small enough for the
+    oracle's dense G, whose gradient G^T W_d^2 (G m - d) is the reference."""
+    import torch
+    from paper_2004_13904_gb300.autograd import g_matmat
+    dt = torch.float64 if dtn == "f64" else torch.float32
+    g = synth.Grid(11, 9, 4, 2, 1, 1, 2)
+    G = oop.dense_G(g, "magnetic", 50.0, 10.0)
+    op = _setup(g, "magnetic", 50.0, 10.0, dt)
+    rng = np.random.default_rng(11)
+    m = 0.1 * rng.random(g.n)
+    d = G @ (0.1 * rng.random(g.n))
+    wd = 1.0 / (0.01 * np.abs(d) + 0.001 * np.abs(d).max())
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    wdt, dwt = t(wd), t(wd * d)
+    x = t(m).requires_grad_(True)
+    r = g_matmat(op, x, rowscale=wdt) - dwt
+    (0.5 * (r.double() * r.double()).sum()).backward()
+    grad = x.grad.double().cpu().numpy()
+    grad_ref = G.T @ (wd * wd * (G @ m - d))
+    assert np.linalg.norm(grad - grad_ref) <= 4 * TOL[dtn] * np.linalg.norm(grad_ref)
+
+    def f_dir(v, h):
+        with torch.no_grad():
+            gx = g_matmat(op, t(m + h * v), rowscale=wdt)
+            rr = (gx - dwt).double()
+            return (0.5 * float((rr * rr).sum()), float(rr.norm()), float(gx.double().norm()))
+
+    V = rng.standard_normal((32, g.n))
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    _fd_check(f_dir, grad, grad_ref, V, 1.0, TOL[dtn])
 
 
 def test_transpose_function_gradients():

@@ -9,7 +9,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("k,length", [(1, 1000), (37, 100003), (2500, 4097)])
 def test_rows_dot_and_axpy(dtn, tol, k, length):
     import torch
-    from paper_2004_13904_gb300.irls import _rows_axpy, _rows_dot
+    from paper_2004_13904_gb300.irls import rows_axpy as _rows_axpy, rows_dot as _rows_dot
     dt = torch.float64 if dtn == "f64" else torch.float32
     gen = torch.Generator(device="cuda").manual_seed(k)
     A = torch.randn(k, length + 3, generator=gen, device="cuda", dtype=dt)[:, :length]
