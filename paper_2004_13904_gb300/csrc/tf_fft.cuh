@@ -192,6 +192,96 @@ template <bool INV, typename C> struct Dft<14, INV, C> {
   }
 };
 
+// cos and sin of 2 pi m / R as compile-time constants.  The fraction m / R is reduced,
+// in integers, to an angle in [0, pi/4] by the symmetries of the circle, whose sine and
+// cosine are then summed from their Taylor series (terms to x^27, below 1e-18 there).
+namespace trig {
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int k = 1; k <= 13; ++k) { t *= -x * x / ((2.0 * k) * (2.0 * k + 1.0)); s += t; }
+  return s;
+}
+constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int k = 1; k <= 13; ++k) { t *= -x * x / ((2.0 * k - 1.0) * (2.0 * k)); s += t; }
+  return s;
+}
+// (cos, sin)(2 pi num / den) for 0 <= num / den <= 1/8 is the Taylor pair; larger
+// fractions fold onto it: f -> 1 - f (sin flips), f -> 1/2 - f (cos flips), f -> 1/4 - f
+// (cos and sin swap).
+constexpr double cos_frac(long long num, long long den, bool want_sin) {
+  num %= den;
+  if (num < 0) num += den;
+  double sign = 1.0;
+  if (2 * num > den) {            // f in (1/2, 1): cos(2 pi f) = cos(2 pi (1 - f))
+    num = den - num;
+    if (want_sin) sign = -sign;
+  }
+  if (4 * num > den) {            // f in (1/4, 1/2]: cos = -cos(2 pi (1/2 - f)), sin same
+    num = den - 2 * num;
+    den *= 2;
+    if (!want_sin) sign = -sign;
+  }
+  if (8 * num > den) {            // f in (1/8, 1/4]: cos = sin(2 pi (1/4 - f)) and vice versa
+    num = den - 4 * num;
+    den *= 4;
+    want_sin = !want_sin;
+  }
+  const double x = kTwoPi * (double)num / (double)den;
+  return sign * (want_sin ? taylor_sin(x) : taylor_cos(x));
+}
+constexpr double cos2pi(int m, int R) { return cos_frac(m, R, false); }
+constexpr double sin2pi(int m, int R) { return cos_frac(m, R, true); }
+}  // namespace trig
+
+// Radix R = P Q from length-P and length-Q transforms (Cooley-Tukey within a thread):
+// X[k1 + P k2] = sum_n2 w_Q^(n2 k2) w_R^(n2 k1) sum_n1 w_P^(n1 k1) x[Q n1 + n2].
+// Twiddles w_R^m = exp(-+ 2 pi i m / R) are compile-time constants; multiples of a
+// quarter turn are applied as sign swaps.
+template <int P, int Q, bool INV, typename C> struct DftPQ {
+  static __device__ __forceinline__ void run(C* v) {
+    typedef decltype(C::x) T;
+    constexpr int R = P * Q;
+    C y[Q][P];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) y[n2][n1] = v[Q * n1 + n2];
+      Dft<P, INV, C>::run(y[n2]);
+#pragma unroll
+      for (int k1 = 1; k1 < P; ++k1) {
+        const int m = (n2 * k1) % R;
+        if (m == 0) continue;
+        const C a = y[n2][k1];
+        if (4 * m == R) {              // w = -+i
+          y[n2][k1] = mul_mi<INV>(a);
+        } else if (2 * m == R) {       // w = -1
+          y[n2][k1] = mk<C>(-a.x, -a.y);
+        } else if (4 * m == 3 * R) {   // w = +-i
+          y[n2][k1] = mul_mi<!INV>(a);
+        } else {
+          const T c = T(trig::cos2pi(m, R)), s = T(trig::sin2pi(m, R));
+          y[n2][k1] = cmul(a, mk<C>(c, INV ? s : -s));
+        }
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      C z[Q];
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) z[n2] = y[n2][k1];
+      Dft<Q, INV, C>::run(z);
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = z[k2];
+    }
+  }
+};
+template <bool INV, typename C> struct Dft<20, INV, C> : DftPQ<4, 5, INV, C> {};
+template <bool INV, typename C> struct Dft<25, INV, C> : DftPQ<5, 5, INV, C> {};
+template <bool INV, typename C> struct Dft<28, INV, C> : DftPQ<4, 7, INV, C> {};
+template <bool INV, typename C> struct Dft<32, INV, C> : DftPQ<4, 8, INV, C> {};
+
 constexpr int kMaxPass = 16;
 
 // A 1-D transform of length n as np radix passes.  Pass p has radix radix[p], stride
