@@ -50,7 +50,7 @@ typedef enum {
   TF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed               */
   TF_EUNSUPPORTED = 4,  /* valid but outside what the library supports (FFT size)   */
   TF_ENOTCONV = 5,      /* reserved for iterative drivers                            */
-  TF_ETIMEOUT = 6       /* reserved for bounded device-side waits                    */
+  TF_ETIMEOUT = 6       /* a bounded device-side wait ran out (tf_batch_persistent)   */
 } tf_status;
 
 typedef enum { TF_F32 = 0, TF_F64 = 1 } tf_dtype;
@@ -304,6 +304,44 @@ tf_status tf_batch_create(tf_op* const* ops, int count, int streams, tf_batch** 
 tf_status tf_batch_destroy(tf_batch* batch);
 tf_status tf_batch_products(tf_batch* batch, int64_t B, const void* const* X, void* const* D,
                             const void* const* Y, void* const* XT, int use_graph, tf_stream stream);
+
+/* One persistent launch for the whole batch (App. A applied per problem).  Every
+ * operator's G X and G^T Y (as in tf_batch_products; operators of one dtype) run in a
+ * single kernel over a work list of column tiles: resident CTAs claim tiles in order from
+ * a device counter, rows stage before column stage before rows stage for each problem,
+ * direction and column, on the generic FFT engine (each operator's radix plans, see
+ * tf_set_radices).  The batch owns a workspace for both directions of every problem
+ * (allocated for B columns on first use and grown for larger B).  A tile that needs an
+ * earlier stage waits for it on the device; every wait is bounded by wait_ms (from the
+ * CTA's start): past it the kernel records TF_ETIMEOUT in a status word and all CTAs
+ * return, leaving the outputs incomplete.  gate, if not NULL, is a DEVICE int that must
+ * become nonzero before any tile starts (a start signal from elsewhere; it waits under the
+ * same bound).  With use_graph the zeroing of the control words and the launch are
+ * recorded once as a CUDA graph and replayed while the key (B, pointers, operator set-ups,
+ * options) is unchanged.  The call synchronises `stream` to read the status.
+ * Errors: TF_EINVAL (mixed dtypes, bad options, a tile pair not compiled: FP32 8x8,
+ * 16x8, 8x4, 4x8; FP64 4x4, 8x8), TF_ETIMEOUT, TF_ENOMEM, TF_ECUDA. */
+typedef struct {
+  int rows_tile, cols_tile; /* sequence pairs / k1 columns per tile; 0: 8x8 (FP32), 4x4 (FP64) */
+  int claim;                /* tiles a CTA claims at once (0: 2)                              */
+  double wait_ms;           /* bound of every device-side wait (<= 0: 2000 ms)                */
+  const int* gate;          /* DEVICE start gate or NULL                                       */
+  int use_graph;            /* record once and replay                                          */
+} tf_batch_opts;
+tf_status tf_batch_persistent(tf_batch* batch, int64_t B, const void* const* X, void* const* D,
+                              const void* const* Y, void* const* XT, const tf_batch_opts* opts,
+                              tf_stream stream);
+
+/* Radix order of the generic engine's plan along x (axis 0, length n1) or y (axis 1,
+ * length n2): radices from {2, 3, 4, 5, 7, 8} whose product is the length, applied in the
+ * given order (each order is a different Stockham pass sequence with its own twiddle
+ * table, same transform).  Used by the generic engine (tf_set_engine(op, 1), lengths
+ * without a compiled plan, tf_matvec_noalloc and the persistent batch); the compiled
+ * plans keep their own.  Waits for the device to be idle.  Errors: TF_EINVAL (axis,
+ * radices, product), TF_ENOMEM, TF_ECUDA.  tf_get_radices writes the current order
+ * (up to 16 entries) and its length. */
+tf_status tf_set_radices(tf_op* op, int axis, const int* radices, int count);
+tf_status tf_get_radices(const tf_op* op, int axis, int* radices, int* count);
 
 /* Host helpers of the projected solves (no GPU involved; exported for tests).
  *

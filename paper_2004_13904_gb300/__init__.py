@@ -243,6 +243,18 @@ class Operator:
                                             ctypes.byref(c)))
         return a.value, b.value, c.value
 
+    def set_radices(self, axis: int, radices):
+        """Radix order of the generic engine's plan along x (axis 0) or y (axis 1)."""
+        r = list(radices)
+        arr = (ctypes.c_int * len(r))(*r)
+        _lib.check(_lib.lib().tf_set_radices(self._h, int(axis), arr, len(r)))
+
+    def radices(self, axis: int):
+        arr = (ctypes.c_int * 16)()
+        n = ctypes.c_int()
+        _lib.check(_lib.lib().tf_get_radices(self._h, int(axis), arr, ctypes.byref(n)))
+        return tuple(arr[:n.value])
+
     def set_engine(self, engine: int):
         """0: compile-time FFT plans where available (default); 1: generic engine."""
         _lib.check(_lib.lib().tf_set_engine(self._h, int(engine)))

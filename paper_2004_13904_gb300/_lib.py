@@ -41,6 +41,12 @@ class tf_irls_report(ctypes.Structure):
                 ("seconds", ctypes.POINTER(ctypes.c_double))]
 
 
+class tf_batch_opts(ctypes.Structure):
+    _fields_ = [("rows_tile", ctypes.c_int), ("cols_tile", ctypes.c_int), ("claim", ctypes.c_int),
+                ("wait_ms", ctypes.c_double), ("gate", ctypes.c_void_p),
+                ("use_graph", ctypes.c_int)]
+
+
 class TFError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -85,6 +91,9 @@ SIGNATURES = {
     "tf_batch_destroy": [vp],
     "tf_batch_products": [vp, i64, P(vp), P(vp), P(vp), P(vp), c_int, vp],
     "tf_damped_bidiag_solve": [c_int, vp, vp, ctypes.c_double, ctypes.c_double, vp],
+    "tf_batch_persistent": [vp, i64, P(vp), P(vp), P(vp), P(vp), P(tf_batch_opts), vp],
+    "tf_set_radices": [vp, c_int, P(c_int), c_int],
+    "tf_get_radices": [vp, c_int, P(c_int), P(c_int)],
 }
 
 

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtf.so")
-SOURCES = ["tf_api.cu", "tf_kernels.cu", "tf_ct_f32.cu", "tf_ct_f64.cu", "tf_irls.cu", "tf_batch.cu"]
+SOURCES = ["tf_api.cu", "tf_kernels.cu", "tf_ct_f32.cu", "tf_ct_f64.cu", "tf_irls.cu", "tf_batch.cu",
+           "tf_batch_f32.cu", "tf_batch_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

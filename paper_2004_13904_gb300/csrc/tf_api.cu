@@ -842,6 +842,42 @@ tf_status tf_set_tuning(tf_op* op, int rows_tile, int cols_tile, int64_t chunk_c
   return TF_OK;
 }
 
+tf_status tf_set_radices(tf_op* op, int axis, const int* radices, int count) {
+  if (check_op(op)) return TF_EINVAL;
+  if (axis != 0 && axis != 1) return fail(TF_EINVAL, "axis must be 0 (x) or 1 (y)");
+  if (!radices || count < 1 || count > tfk::kMaxPass)
+    return fail(TF_EINVAL, "need 1 to %d radices", tfk::kMaxPass);
+  const int n = axis == 0 ? op->n1 : op->n2;
+  int prod = 1;
+  std::vector<int> rad(radices, radices + count);
+  for (int r : rad) {
+    if (r != 2 && r != 3 && r != 4 && r != 5 && r != 7 && r != 8)
+      return fail(TF_EINVAL, "radix %d is not one of 2, 3, 4, 5, 7, 8", r);
+    prod *= r;
+  }
+  if (prod != n) return fail(TF_EINVAL, "radices multiply to %d, the transform length is %d", prod, n);
+  HostPlan h = make_plan_from(n, rad);
+  void* tw = nullptr;
+  tf_status st = upload_twiddles(h, op->dtype, &tw);
+  if (st != TF_OK) { cudaFree(tw); return st; }
+  cudaDeviceSynchronize();   // no product of this operator may still use the old table
+  void*& old = axis == 0 ? op->tw1 : op->tw2;
+  cudaFree(old);
+  old = tw;
+  (axis == 0 ? op->p1 : op->p2) = h;
+  return TF_OK;
+}
+
+tf_status tf_get_radices(const tf_op* op, int axis, int* radices, int* count) {
+  if (check_op(op)) return TF_EINVAL;
+  if ((axis != 0 && axis != 1) || !radices || !count)
+    return fail(TF_EINVAL, "axis must be 0 or 1, radices and count non-NULL");
+  const tfk::FftPlan& p = axis == 0 ? op->p1.plan : op->p2.plan;
+  for (int i = 0; i < p.np; ++i) radices[i] = p.radix[i];
+  *count = p.np;
+  return TF_OK;
+}
+
 tf_status tf_set_engine(tf_op* op, int engine) {
   if (check_op(op)) return TF_EINVAL;
   if (engine != 0 && engine != 1) return fail(TF_EINVAL, "engine must be 0 or 1");
@@ -891,10 +927,12 @@ tf_status tf_profile_read(tf_op* op, double* ms, int64_t* launches, int64_t* col
 }
 
 tf_status tf_debug_oob(int* checked, int* site, int64_t* offset, int64_t* extent) {
-  tfk::OobRecord recs[3];
+  tfk::OobRecord recs[5];
   bool ok = tfk::oob_read_generic(&recs[0], true);
   ok = tfk::oob_read_ct_f32(&recs[1], true) && ok;
   ok = tfk::oob_read_ct_f64(&recs[2], true) && ok;
+  ok = tfk::oob_read_batch_f32(&recs[3], true) && ok;
+  ok = tfk::oob_read_batch_f64(&recs[4], true) && ok;
   if (checked) *checked = ok ? 1 : 0;
   if (site) *site = 0;
   if (offset) *offset = 0;
@@ -968,8 +1006,57 @@ tf_status op_info(const tf_op* op, OpInfo* out) {
   return TF_OK;
 }
 
+OpGeneric op_generic(const tf_op* op) {
+  OpGeneric g;
+  g.dtype = op->dtype;
+  g.m = op->m();
+  g.n = op->n();
+  g.w1_per_col = op->w1_per_col();
+  g.w2_per_col = op->w2_per_col();
+  g.csize = op->csize();
+  g.n1 = op->n1;
+  g.n2 = op->n2;
+  g.tw1 = op->p1.plan.tw_count;
+  g.tw2 = op->p2.plan.tw_count;
+  g.rows_model = op->nz * op->ny;
+  g.rows_data = op->sy;
+  g.nh = op->nh;
+  return g;
+}
+
+template <typename T>
+void op_product_stages(const tf_op* op, const T* X, T* D, const T* Y, T* XT, void* fw1, void* fw2,
+                       void* aw1, void* aw2, ProductStages<T>* out) {
+  typedef typename CT<T>::C C;
+  const C* tw1 = (const C*)op->tw1;
+  const C* tw2 = (const C*)op->tw2;
+  ProductStages<T>& o = *out;
+  o.f0.src = X; o.f0.src_ld = op->n(); o.f0.row_len = op->nx; o.f0.nrows = op->nz * op->ny;
+  o.f0.seq_off = 0; o.f0.scale = nullptr; o.f0.dst = (C*)fw1; o.f0.dst_ld = op->w1_per_col();
+  o.f0.nh = op->nh; o.f0.hs = op->hs; o.f0.plan = op->p1.plan; o.f0.tw = tw1;
+  o.f1.z = (const C*)fw1; o.f1.z_ld = op->w1_per_col(); o.f1.spec = (const C*)op->spec;
+  o.f1.s = (C*)fw2; o.f1.s_ld = op->w2_per_col(); o.f1.nh = op->nh; o.f1.hs = op->hs;
+  o.f1.ny = op->ny; o.f1.sy = op->sy; o.f1.nz = op->nz; o.f1.plan = op->p2.plan; o.f1.tw = tw2;
+  o.f2.src = (const C*)fw2; o.f2.src_ld = op->w2_per_col(); o.f2.nh = op->nh; o.f2.hs = op->hs;
+  o.f2.nrows = op->sy; o.f2.dst = D; o.f2.dst_ld = op->m(); o.f2.out_len = op->sx;
+  o.f2.seq_off = op->nx - 1; o.f2.scale = nullptr; o.f2.plan = op->p1.plan; o.f2.tw = tw1;
+  o.a0.src = Y; o.a0.src_ld = op->m(); o.a0.row_len = op->sx; o.a0.nrows = op->sy;
+  o.a0.seq_off = op->nx - 1; o.a0.scale = nullptr; o.a0.dst = (C*)aw2; o.a0.dst_ld = op->w2_per_col();
+  o.a0.nh = op->nh; o.a0.hs = op->hs; o.a0.plan = op->p1.plan; o.a0.tw = tw1;
+  o.a1.z = (const C*)aw2; o.a1.z_ld = op->w2_per_col(); o.a1.spec = (const C*)op->spec;
+  o.a1.u = (C*)aw1; o.a1.u_ld = op->w1_per_col(); o.a1.nh = op->nh; o.a1.hs = op->hs;
+  o.a1.ny = op->ny; o.a1.sy = op->sy; o.a1.nz = op->nz; o.a1.plan = op->p2.plan; o.a1.tw = tw2;
+  o.a2.src = (const C*)aw1; o.a2.src_ld = op->w1_per_col(); o.a2.nh = op->nh; o.a2.hs = op->hs;
+  o.a2.nrows = op->nz * op->ny; o.a2.dst = XT; o.a2.dst_ld = op->n(); o.a2.out_len = op->nx;
+  o.a2.seq_off = 0; o.a2.scale = nullptr; o.a2.plan = op->p1.plan; o.a2.tw = tw1;
+}
+template void op_product_stages<float>(const tf_op*, const float*, float*, const float*, float*,
+                                       void*, void*, void*, void*, ProductStages<float>*);
+template void op_product_stages<double>(const tf_op*, const double*, double*, const double*,
+                                        double*, void*, void*, void*, void*, ProductStages<double>*);
+
 OpLaunchKey op_launch_key(const tf_op* op) {
-  return OpLaunchKey{op->w1, op->chunk, op->engine, op->rows_tile, op->cols_tile};
+  return OpLaunchKey{op->w1, op->chunk, op->engine, op->rows_tile, op->cols_tile, op->tw1, op->tw2};
 }
 
 tf_status api_fail(tf_status st, const char* fmt, ...) {

@@ -1,0 +1,20 @@
+// Persistent batch kernel instantiated for double data (tile pairs rows x columns:
+// 4 x 4, 8 x 8).
+#include "tf_batch_kernels.cuh"
+
+namespace tfk {
+
+template <>
+cudaError_t launch_batch<double>(const BatchCtl& c, int tb, int tk, size_t smem, cudaStream_t s,
+                            int* grid) {
+  typedef double T;
+  switch (tb * 100 + tk) {
+    TF_BATCH_CASE(4, 4)
+    TF_BATCH_CASE(8, 8)
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+TF_DEFINE_OOB_READER(oob_read_batch_f64)
+
+}  // namespace tfk

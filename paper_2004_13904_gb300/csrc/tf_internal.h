@@ -49,6 +49,66 @@ template <typename T> struct ColsAdj {
   FftPlan plan; const typename CT<T>::C* tw;
 };
 
+// ---- persistent batch kernel (tf_batch_kernels.cu) ----------------------------------
+//
+// One launch runs the generic engine's product stages of many problems.  The work items
+// are tiles of columns; a segment is one stage of one problem and direction, a
+// contiguous range of items (column-major: item = first + col * tiles + tile).  Items
+// are claimed in increasing order, and a stage's items come after those of the stage it
+// waits on, so every wait is for items already claimed by running CTAs.
+struct BatchSeg {
+  long long first;   // first work item of the segment
+  int kind;          // 0 rows_r2c, 1 cols_fwd, 2 rows_c2r, 3 cols_adj
+  int tiles;         // tiles per column
+  int cols;          // columns
+  int args;          // index of the stage's arguments
+  int wait;          // counters (one per column) of the stage this one needs, -1 if none
+  int wait_target;   // tiles per column of that stage
+  int count;         // counters (one per column) this stage's finished tiles add to
+};
+template <typename T> union BatchArgs {
+  RowsR2C<T> r2c;
+  ColsFwd<T> fwd;
+  RowsC2R<T> c2r;
+  ColsAdj<T> adj;
+};
+struct BatchCtl {
+  unsigned long long* work;  // next unclaimed item (zero at launch)
+  int* counters;             // finished tiles per (segment, column) (zero at launch)
+  int* status;               // 0 at launch; 6 (TF_ETIMEOUT) once a wait ran out
+  const int* gate;           // NULL, or: no item starts before *gate != 0
+  long long total;           // work items
+  int nseg;
+  const BatchSeg* seg;       // nseg segments in increasing `first`
+  const void* args;          // BatchArgs<T>[]
+  unsigned long long budget_ns;  // every wait gives up this long after the CTA started
+  int claim;                 // items a CTA claims at once
+};
+// Launches the persistent kernel with rows tile tb and column tile tk (4, 8 or 16) and
+// `smem` bytes of dynamic shared memory (the largest stage's need), one grid of resident
+// CTAs; *grid receives its size.
+// Returns cudaErrorInvalidValue for a tile pair the dtype was not compiled with (FP32:
+// 8x8, 16x8, 8x4, 4x8; FP64: 4x4, 8x8).
+template <typename T>
+cudaError_t launch_batch(const BatchCtl& c, int tb, int tk, size_t smem, cudaStream_t s, int* grid);
+template <> cudaError_t launch_batch<float>(const BatchCtl&, int, int, size_t, cudaStream_t, int*);
+template <> cudaError_t launch_batch<double>(const BatchCtl&, int, int, size_t, cudaStream_t, int*);
+
+// The generic engine's six stage arguments of one operator's products on columns of
+// X / D / Y / XT (leading dimensions n and m): G X (rows_r2c, cols_fwd, rows_c2r) through
+// the workspace columns fw1 / fw2 and G^T Y (rows_r2c, cols_adj, rows_c2r) through aw1 /
+// aw2 (workspace column strides as the operator's own workspace).  Defined in tf_api.cu.
+template <typename T> struct ProductStages {
+  RowsR2C<T> f0; ColsFwd<T> f1; RowsC2R<T> f2;
+  RowsR2C<T> a0; ColsAdj<T> a1; RowsC2R<T> a2;
+};
+struct OpGeneric {
+  int dtype;                     // tf_dtype
+  int64_t m, n, w1_per_col, w2_per_col;
+  size_t csize;
+  int n1, n2, tw1, tw2, rows_model, rows_data, nh;
+};
+
 struct TableArgs {
   int kind;                // 0 gravity, 1 magnetic
   int n1min, n2min, nz, nx, ny, pxl, pyl;
@@ -100,6 +160,8 @@ int ct_menu_cols_radices(int n, int* radices /* up to kMaxPass */);
 bool oob_read_generic(OobRecord* out, bool clear);
 bool oob_read_ct_f32(OobRecord* out, bool clear);
 bool oob_read_ct_f64(OobRecord* out, bool clear);
+bool oob_read_batch_f32(OobRecord* out, bool clear);
+bool oob_read_batch_f64(OobRecord* out, bool clear);
 
 cudaError_t launch_table(const TableArgs& a, cudaStream_t s);
 // Re-orthogonalisation helpers on a stack of k vectors A[j*lda + i] (dtype 0: float,

@@ -60,8 +60,10 @@ def test_tuner_choice_keeps_results():
     op = _ops(torch.float64, 1)[0]
     X = torch.randn(7, op.n, device="cuda", dtype=torch.float64)
     ref = op.matmat(X)
-    engine, chunk = tune(op, 7)
+    engine, chunk, rx, ry = tune(op, 7)
     assert engine in (0, 1) and 1 <= chunk <= 7
+    assert op.radices(0) == tuple(rx) and op.radices(1) == tuple(ry)
+    assert int(np.prod(rx)) == op.n1 and int(np.prod(ry)) == op.n2
     assert (op.n1, op.n2, op.nz, str(op.dtype), 7) in TUNE_CACHE
     assert torch.allclose(op.matmat(X), ref, rtol=0, atol=1e-12 * ref.abs().max())
 
