@@ -367,13 +367,17 @@ def main():
         Yh.copy_(Y)
         Dh = torch.empty((B, g.m), dtype=dt, pin_memory=True)
         XTh = torch.empty((B, g.n), dtype=dt, pin_memory=True)
-        op.products_host(Xh, Yh, Dh, XTh, chunks=args.e2e_chunks)
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        for _ in range(2):   # the first calls pay one-time costs (staging allocation, mappings)
             op.products_host(Xh, Yh, Dh, XTh, chunks=args.e2e_chunks)
             torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        step_ms = []
+        for _ in range(args.e2e_steps):
+            t1 = time.perf_counter()
+            op.products_host(Xh, Yh, Dh, XTh, chunks=args.e2e_chunks)
+            torch.cuda.synchronize()
+            step_ms.append(round(1e3 * (time.perf_counter() - t1), 2))
         e2e_s = time.perf_counter() - t0
         barrier()
         e2e_s = max_over_ranks(e2e_s, dev)
@@ -381,7 +385,7 @@ def main():
                "h2d_bytes_per_step": (g.n + g.m) * B * esz,
                "d2h_bytes_per_step": (g.m + g.n) * B * esz,
                "call": "tf_products_host (C ABI), pinned host blocks, "
-                       f"{args.e2e_chunks} chunks per step"}
+                       f"{args.e2e_chunks} chunks per step", "step_ms": step_ms}
         del Xh, Yh, Dh, XTh
 
     # roofline of the dominant kernel, timed live with events on the launching stream

@@ -65,8 +65,9 @@ __device__ __forceinline__ void ld_row_vec(const C* p, int k1, int nh, bool ok, 
 // Register budgets of the column kernels, as a minimum number of resident CTAs per SM
 // for __launch_bounds__ (measured with 1260-column blocks at transform lengths 64 to
 // 512: the single-precision forward kernel is fastest near 128 registers a thread, the
-// adjoint near 100, and near 85 at n >= 448; the double kernels are indifferent).  The row kernels keep the compiler's
-// default budget, which measured fastest for them.
+// adjoint near 100, and near 85 at n >= 448; the double kernels are indifferent).  At
+// c4 (2510-column blocks) the tighter budgets spill and lose: cols_fwd at 768 threads
+// per SM 16.1 -> 18.6 ms per step, cols_adj at 1024 14.6 -> 17.3 ms.
 template <typename T> constexpr int cols_min_blocks(int nt, int threads_per_sm) {
   return std::is_same<T, float>::value && threads_per_sm / nt > 1 ? threads_per_sm / nt : 1;
 }
@@ -102,17 +103,17 @@ __device__ __forceinline__ void visit_pairs(int E, const Body& body) {
 // over (element, pair group) go through visit_pairs.
 // ZHI: the rows' data lies in [0, N/2) of the sequence, so staging fills only that half
 // and the first pass takes the upper half as zero.
-// Minimum resident CTAs per SM requested for the row kernels (1: the compiler's default
-// register budget).
-#ifndef TF_CT_ROWS_MINB
-#define TF_CT_ROWS_MINB 1
-#endif
-template <typename T> constexpr int rows_min_blocks(int nt) {
-  return std::is_same<T, float>::value && nt == 256 ? TF_CT_ROWS_MINB : 1;
+// Register budgets of the single-precision row kernels at n > 256 (256-thread CTAs), as
+// resident threads per SM for __launch_bounds__: 1536 for rows_r2c (40 registers) and 1280
+// for rows_c2r (48).  Measured on 2510-column c4 blocks against the compiler's default
+// budget (55 registers, 1024 threads): rows_r2c 10.7 -> 7.9 ms and rows_c2r 10.9 -> 8.4 ms
+// per step; the two kernels wait on memory, and more resident CTAs overlap those waits.
+template <typename T> constexpr int rows_min_blocks(int nt, int threads_per_sm) {
+  return std::is_same<T, float>::value && nt == 256 ? threads_per_sm / nt : 1;
 }
 
 template <typename T, class P, int TB, int V, int NT, bool ZHI>
-__global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT)) k_rows_r2c(const RowsR2C<T> a) {
+__global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT, 1536)) k_rows_r2c(const RowsR2C<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT)) k_rows_r2c(const R
 }
 
 template <typename T, class P, int TB, int V, int NT>
-__global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT)) k_rows_c2r(const RowsC2R<T> a) {
+__global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT, 1280)) k_rows_c2r(const RowsC2R<T> a) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -233,25 +234,6 @@ __global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT)) k_rows_c2r(const R
 // double kernels measured no gain from it).
 template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::value;
 
-// The forward column kernel can stage the next layer's row-transformed tile (rows < ny of
-// the workspace, TB values each) into shared memory with asynchronous copies while the
-// current layer is transformed, so that no pass waits on global memory at a layer start.
-#ifndef TF_CT_FWD_ASYNC
-#define TF_CT_FWD_ASYNC 0
-#endif
-template <typename T> constexpr bool kFwdAsync = TF_CT_FWD_ASYNC && std::is_same<T, float>::value;
-
-// 16-byte asynchronous global -> shared copy (cp.async, cached at L2 only), its group
-// commit and the wait for all but the newest `N` committed groups.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // Column stage of G x (ZHI: ny <= N/2, the layer rows fill the lower half).  In single
 // precision each thread loads the spectrum values that its last forward pass multiplies
 // at the start of every layer, into registers, so that their global-memory latency
@@ -268,50 +250,16 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
   C* acc = buf + N * TB;
-  // with kFwdAsync: two staging tiles of the layer rows, [NSZ][TB] each
-  constexpr bool kAsync = kFwdAsync<T>;
-  constexpr int NSZ = ZHI && P::can_zero_hi ? N / 2 : N;
-  C* zst = acc + N * TB;
   for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  __syncthreads();
   const int k0 = blockIdx.x * TB;
   const int nh = a.nh, hs = a.hs, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
   const int z_ext = a.nz * ny * hs, g_ext = a.nz * N * hs, s_ext = sy * hs;
-  // issues the copies of layer r's rows < ny (TB values each, 16-byte pieces) into slot
-  auto stage_layer = [&](int r, int slot) {
-    constexpr int PIECES = TB * (int)sizeof(C) / 16;
-    C* dst = zst + slot * NSZ * TB;
-    const C* src = z + r * ny * hs + k0;
-    for (int u = threadIdx.x; u < ny * PIECES; u += NT) {
-      const int row = u / PIECES, piece = u - row * PIECES;
-      if (TF_IN(kSiteFwdZ, r * ny * hs + row * hs + k0 + (piece + 1) * 16 / (int)sizeof(C) - 1, z_ext))
-        cp_async16(reinterpret_cast<unsigned char*>(dst + row * TB) + piece * 16,
-                   reinterpret_cast<const unsigned char*>(src + row * hs) + piece * 16);
-    }
-    cp_async_commit();
-  };
-  if constexpr (kAsync) {
-    // rows ny .. NSZ-1 of both tiles stay zero (the copies fill only rows < ny)
-    for (int i = threadIdx.x; i < 2 * NSZ * TB; i += NT) zst[i] = zero<C>();
-    __syncthreads();
-    stage_layer(0, 0);
-  }
-  __syncthreads();
   const C* spec = a.spec;
   C gpre[kPre ? ITL * RL : 1][V];
   for (int r = 0; r < a.nz; ++r) {
     const int zoff = r * ny * hs, goff = r * N * hs;
-    if constexpr (kAsync) {
-      // the next layer's copies go to the slot this layer's predecessor read (all threads
-      // have passed that layer's barriers); then this layer's copies must be complete
-      if (r + 1 < a.nz) {
-        stage_layer(r + 1, (r + 1) & 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncthreads();
-    }
 #pragma unroll
     for (int it = 0; it < ITL; ++it) {
       const int u = threadIdx.x + it * NT;
@@ -330,15 +278,10 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
     // zeroed when allocated, the row kernels never write its padding, and the column
     // kernels write zeros there (their padded sequences have zero inputs).  A masked load
     // measured much slower here (the mask's select waits for the load).
-    const C* zs = zst + (r & 1) * NSZ * TB;
     auto load = [=](int idx, int b0, C* o) {
       const int k1 = k0 + b0;
-      if constexpr (kAsync) {
-        if (TF_IN(kSiteSmem + 4, idx * TB + b0 + V - 1, NSZ * TB)) Vec<V, C>::ld(zs + idx * TB + b0, o);
-      } else {
-        const int e = zoff + idx * hs + k1;
-        ld_row_vec<V, false>(z + e, k1, nh, idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e + V - 1, z_ext), o);
-      }
+      const int e = zoff + idx * hs + k1;
+      ld_row_vec<V, false>(z + e, k1, nh, idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e + V - 1, z_ext), o);
     };
     auto mac = [&](int idx, int b0, const C* v, int slot) {
       C cur[V];
@@ -493,8 +436,7 @@ template <typename T, class P>
 cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
   typedef ColTiles<T, P> TL;
   const bool zhi = P::can_zero_hi && a.ny <= P::n / 2;
-  const int nsz = kFwdAsync<T> ? 2 * (zhi ? P::n / 2 : P::n) : 0;   // staging tiles' rows
-  const size_t sm = (size_t)(twpad(P::n - 1) + (2 * P::n + nsz) * TL::TB) * sizeof(typename CT<T>::C);
+  const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
   const dim3 grid(cdiv(a.nh, TL::TB), ncols);
   if (zhi) return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, true>>(a, grid, TL::NT, sm, s);
   return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, false>>(a, grid, TL::NT, sm, s);

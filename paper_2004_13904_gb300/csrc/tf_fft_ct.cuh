@@ -56,12 +56,14 @@ template <typename C, int TB> __host__ __device__ constexpr int swz(int row) {
   constexpr int rows_per_line = (int)(128 / (TB * sizeof(C))) > 1 ? (int)(128 / (TB * sizeof(C))) : 1;
   return TB >= 4 ? ((row / rows_per_line) & (TB / 2 - 1)) << 1 : 0;
 }
-// Rows of 64 bytes fill half of the 32 banks, the half given by the row's parity.  The
-// first pass of a plan with first radix S stores rows idx and idx + S in the same
-// quarter-warp phase; swapping the rows of each even/odd pair in every other block of S
-// puts those two in different halves.  (A permutation of [0, N) for even N.)
+// Rows of 128/q bytes (q = 2 or 4) fill 1/q of the 32 banks, the part given by the row
+// index mod q.  The first pass of a plan with first radix S stores rows idx, idx + S,
+// idx + 2S, ... in the same quarter-warp phase; XOR-ing the low bits of the row with the
+// block number (idx / S) mod q puts q consecutive blocks in different bank parts.  (A
+// permutation of [0, N) for N divisible by q.)
 template <typename C, int TB, int S = 8> __host__ __device__ constexpr int row_of(int idx) {
-  return TB * sizeof(C) == 64 ? idx ^ ((idx / S) & 1) : idx;
+  constexpr int q = TB * (int)sizeof(C) == 64 ? 2 : TB * (int)sizeof(C) == 32 ? 4 : 1;
+  return q > 1 ? idx ^ ((idx / S) & (q - 1)) : idx;
 }
 template <typename C, int TB, int S = 8> __host__ __device__ __forceinline__ int at(int idx, int b) {
   const int row = row_of<C, TB, S>(idx);

@@ -49,8 +49,10 @@ def _tiles(N, radices, dtype):
 def _at(TB, csize, S):
     rows_per_line = max(128 // (TB * csize), 1)
 
+    q = 2 if TB * csize == 64 else 4 if TB * csize == 32 else 1
+
     def row_of(idx):
-        return idx ^ ((idx // S) & 1) if TB * csize == 64 else idx
+        return idx ^ ((idx // S) & (q - 1)) if q > 1 else idx
 
     def swz(row):
         return ((row // rows_per_line) & (TB // 2 - 1)) << 1 if TB >= 4 else 0
