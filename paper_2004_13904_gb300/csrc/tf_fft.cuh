@@ -140,58 +140,6 @@ template <bool INV, typename C> struct Dft<7, INV, C> {
   static __device__ __forceinline__ void run(C* v) { dft_odd<7, INV>(v); }
 };
 
-// Radix 16 as 4 x 4: length-4 transforms of the four interleaved subsequences, twiddles
-// w16^(n2 k1), then length-4 transforms across them (output k1 + 4 k2).
-template <bool INV, typename C> struct Dft<16, INV, C> {
-  static __device__ __forceinline__ void run(C* v) {
-    typedef decltype(C::x) T;
-    const T c = T(0.9238795325112867), s = T(0.3826834323650898), h = T(0.7071067811865475244008444);
-    // w16^m = (cos(2 pi m / 16), -+ sin(2 pi m / 16)) for m = 0..9
-    const T wc[10] = {T(1), c, h, s, T(0), -s, -h, -c, T(-1), -c};
-    const T ws[10] = {T(0), s, h, c, T(1), c, h, s, T(0), -s};
-    C y[4][4];
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) {
-#pragma unroll
-      for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
-      Dft<4, INV, C>::run(y[n2]);
-#pragma unroll
-      for (int k1 = 1; k1 < 4; ++k1) {
-        const int m = n2 * k1;
-        if (m == 0) continue;
-        y[n2][k1] = cmul(y[n2][k1], mk<C>(wc[m], INV ? ws[m] : -ws[m]));
-      }
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-      C z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
-      Dft<4, INV, C>::run(z);
-#pragma unroll
-      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
-    }
-  }
-};
-// Radix 14 as 2 x 7: length-7 transforms of the even and odd subsequences, twiddles
-// w14^k on the odd one, then a length-2 combination (outputs k and k + 7).
-template <bool INV, typename C> struct Dft<14, INV, C> {
-  static __device__ __forceinline__ void run(C* v) {
-    typedef decltype(C::x) T;
-    const T wc[7] = {T(1.0), T(0.9009688679024191), T(0.6234898018587336), T(0.22252093395631445), T(-0.22252093395631434), T(-0.6234898018587335), T(-0.900968867902419)};
-    const T ws[7] = {T(0.0), T(0.4338837391175581), T(0.7818314824680298), T(0.9749279121818236), T(0.9749279121818236), T(0.7818314824680299), T(0.43388373911755823)};
-    C e[7], o[7];
-#pragma unroll
-    for (int n = 0; n < 7; ++n) { e[n] = v[2 * n]; o[n] = v[2 * n + 1]; }
-    Dft<7, INV, C>::run(e);
-    Dft<7, INV, C>::run(o);
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const C t = k == 0 ? o[0] : cmul(o[k], mk<C>(wc[k], INV ? ws[k] : -ws[k]));
-      v[k] = cadd(e[k], t);
-      v[k + 7] = csub(e[k], t);
-    }
-  }
-};
-
 // cos and sin of 2 pi m / R as compile-time constants.  The fraction m / R is reduced,
 // in integers, to an angle in [0, pi/4] by the symmetries of the circle, whose sine and
 // cosine are then summed from their Taylor series (terms to x^27, below 1e-18 there).
@@ -277,10 +225,10 @@ template <int P, int Q, bool INV, typename C> struct DftPQ {
     }
   }
 };
-template <bool INV, typename C> struct Dft<20, INV, C> : DftPQ<4, 5, INV, C> {};
-template <bool INV, typename C> struct Dft<25, INV, C> : DftPQ<5, 5, INV, C> {};
-template <bool INV, typename C> struct Dft<28, INV, C> : DftPQ<4, 7, INV, C> {};
-template <bool INV, typename C> struct Dft<32, INV, C> : DftPQ<4, 8, INV, C> {};
+// Radix 16 as 4 x 4 (outputs k1 + 4 k2) and radix 14 as 2 x 7 (even and odd
+// subsequences, outputs k and k + 7).
+template <bool INV, typename C> struct Dft<16, INV, C> : DftPQ<4, 4, INV, C> {};
+template <bool INV, typename C> struct Dft<14, INV, C> : DftPQ<7, 2, INV, C> {};
 
 constexpr int kMaxPass = 16;
 
