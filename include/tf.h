@@ -257,7 +257,9 @@ tf_status tf_peak_probe(tf_dtype dtype, double* tflops, tf_stream stream);
  * allocate their own device workspace (A: t_p x n and H: (t_p+1) x m for tf_gkb; five
  * t_p x max(n, m) blocks for tf_rsvd), run on `stream`, and synchronise it before
  * returning.  The projected problems are solved on the host in FP64.  tf_rsvd uses
- * cuSOLVER (QR, symmetric eigen-decomposition) and cuBLAS (B^T B).  Errors: TF_EINVAL
+ * cuSOLVER (QR, symmetric eigen-decomposition) and cuBLAS (B^T B); a basis block above
+ * 2^30 values (c4: 10^6 x 2510) is factored as a tall-skinny QR of row blocks below that
+ * size, which needs two more buffers of one row block each.  Errors: TF_EINVAL
  * (bad sizes or parameters, t > t_p, tf_rsvd with t_p > min(m, n)), TF_ENOMEM, TF_ECUDA,
  * TF_ENOTCONV (the host eigenvalue iteration did not converge). */
 typedef struct {

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <numeric>
 #include <vector>
@@ -511,32 +512,130 @@ struct Handles {
   }
 };
 
-// Rows of Y (k x len, row-major = column-major len x k) replaced by an orthonormal basis
-// of their span (economic QR of Y^T, Q kept).  Needs k <= len.
-tf_status qr_rows(Handles& h, DevMem& mem, float* Y, int64_t len, int k) {
+// Typed cuSOLVER / cuBLAS entry points of the QR pieces.
+int geqrf_lwork(cusolverDnHandle_t h, int m, int n, float* A, int lda, int* lw) {
+  return (int)cusolverDnSgeqrf_bufferSize(h, m, n, A, lda, lw);
+}
+int geqrf_lwork(cusolverDnHandle_t h, int m, int n, double* A, int lda, int* lw) {
+  return (int)cusolverDnDgeqrf_bufferSize(h, m, n, A, lda, lw);
+}
+int orgqr_lwork(cusolverDnHandle_t h, int m, int n, float* A, int lda, const float* tau, int* lw) {
+  return (int)cusolverDnSorgqr_bufferSize(h, m, n, n, A, lda, tau, lw);
+}
+int orgqr_lwork(cusolverDnHandle_t h, int m, int n, double* A, int lda, const double* tau, int* lw) {
+  return (int)cusolverDnDorgqr_bufferSize(h, m, n, n, A, lda, tau, lw);
+}
+int geqrf(cusolverDnHandle_t h, int m, int n, float* A, int lda, float* tau, float* w, int lw, int* info) {
+  return (int)cusolverDnSgeqrf(h, m, n, A, lda, tau, w, lw, info);
+}
+int geqrf(cusolverDnHandle_t h, int m, int n, double* A, int lda, double* tau, double* w, int lw, int* info) {
+  return (int)cusolverDnDgeqrf(h, m, n, A, lda, tau, w, lw, info);
+}
+int orgqr(cusolverDnHandle_t h, int m, int n, float* A, int lda, const float* tau, float* w, int lw, int* info) {
+  return (int)cusolverDnSorgqr(h, m, n, n, A, lda, tau, w, lw, info);
+}
+int orgqr(cusolverDnHandle_t h, int m, int n, double* A, int lda, const double* tau, double* w, int lw, int* info) {
+  return (int)cusolverDnDorgqr(h, m, n, n, A, lda, tau, w, lw, info);
+}
+int gemm_nn(cublasHandle_t h, int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C,
+            int ldc) {
+  const float one = 1.0f, zero = 0.0f;
+  return (int)cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc);
+}
+int gemm_nn(cublasHandle_t h, int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+            double* C, int ldc) {
+  const double one = 1.0, zero = 0.0;
+  return (int)cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc);
+}
+
+// The k x k upper triangle of src (ld lds) into dst (ld ldd), zeros below the diagonal.
+template <typename T>
+__global__ void k_copy_upper(T* dst, int64_t ldd, const T* src, int64_t lds, int k) {
+  const int64_t total = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % k), c = (int)(e / k);
+    dst[r + c * ldd] = r <= c ? src[r + c * lds] : T(0);
+  }
+}
+
+// Blocks handed to one cuSOLVER / cuBLAS call stay below 2^30 elements (their 32-bit
+// interfaces index matrices with int).  TF_QR_BLOCK_ELEMS lowers the bound (tests use it
+// to take the tall-skinny path on small problems).
+int64_t qr_max_elems() {
+  const int64_t cap = (int64_t)1 << 30;
+  const char* v = getenv("TF_QR_BLOCK_ELEMS");
+  if (!v) return cap;
+  const long long x = atoll(v);
+  return x >= 1 && x < cap ? (int64_t)x : cap;
+}
+
+// Householder QR of the column-major len x k block Y (ld = len) in place, Q kept.
+template <typename T>
+tf_status qr_inplace(Handles& h, DevMem& mem, T* Y, int64_t len, int k) {
+  if (len * k > ((int64_t)1 << 30)) return api_fail(TF_EUNSUPPORTED, "QR block of %lld x %d too large", (long long)len, k);
   int lw1 = 0, lw2 = 0;
-  TRY_LIB(cusolverDnSgeqrf_bufferSize(h.sol, (int)len, k, Y, (int)len, &lw1), "geqrf buffer");
-  float *tau, *work;
+  T *tau, *work;
   int* info;
   TRY_CUDA(mem.get(&tau, k), "cudaMalloc(QR)");
   TRY_CUDA(mem.get(&info, 1), "cudaMalloc(QR)");
-  TRY_LIB(cusolverDnSorgqr_bufferSize(h.sol, (int)len, k, k, Y, (int)len, tau, &lw2), "orgqr buffer");
+  TRY_LIB(geqrf_lwork(h.sol, (int)len, k, Y, (int)len, &lw1), "geqrf buffer");
+  TRY_LIB(orgqr_lwork(h.sol, (int)len, k, Y, (int)len, tau, &lw2), "orgqr buffer");
   TRY_CUDA(mem.get(&work, std::max(lw1, lw2)), "cudaMalloc(QR)");
-  TRY_LIB(cusolverDnSgeqrf(h.sol, (int)len, k, Y, (int)len, tau, work, std::max(lw1, lw2), info), "geqrf");
-  TRY_LIB(cusolverDnSorgqr(h.sol, (int)len, k, k, Y, (int)len, tau, work, std::max(lw1, lw2), info), "orgqr");
+  TRY_LIB(geqrf(h.sol, (int)len, k, Y, (int)len, tau, work, std::max(lw1, lw2), info), "geqrf");
+  TRY_LIB(orgqr(h.sol, (int)len, k, Y, (int)len, tau, work, std::max(lw1, lw2), info), "orgqr");
   return TF_OK;
 }
-tf_status qr_rows(Handles& h, DevMem& mem, double* Y, int64_t len, int k) {
-  int lw1 = 0, lw2 = 0;
-  TRY_LIB(cusolverDnDgeqrf_bufferSize(h.sol, (int)len, k, Y, (int)len, &lw1), "geqrf buffer");
-  double *tau, *work;
-  int* info;
-  TRY_CUDA(mem.get(&tau, k), "cudaMalloc(QR)");
-  TRY_CUDA(mem.get(&info, 1), "cudaMalloc(QR)");
-  TRY_LIB(cusolverDnDorgqr_bufferSize(h.sol, (int)len, k, k, Y, (int)len, tau, &lw2), "orgqr buffer");
-  TRY_CUDA(mem.get(&work, std::max(lw1, lw2)), "cudaMalloc(QR)");
-  TRY_LIB(cusolverDnDgeqrf(h.sol, (int)len, k, Y, (int)len, tau, work, std::max(lw1, lw2), info), "geqrf");
-  TRY_LIB(cusolverDnDorgqr(h.sol, (int)len, k, k, Y, (int)len, tau, work, std::max(lw1, lw2), info), "orgqr");
+
+// Buffers of the tall QR, allocated on first use and kept for the driver's later steps.
+template <typename T> struct QrWork {
+  T *W = nullptr, *W2 = nullptr, *Rs = nullptr, *tau = nullptr, *work = nullptr;
+  int* info = nullptr;
+  int lwork = 0;
+};
+
+// Rows of Y (k x len, row-major = column-major len x k) replaced by an orthonormal basis
+// of their span (economic QR of Y^T, Q kept).  Needs k <= len.  A block above
+// qr_max_elems() elements is factored as a tall-skinny QR: its nb row blocks Y_i = Q_i R_i each, the stacked
+// [R_1; ...; R_nb] = Q_s R once more, and Q = diag(Q_i) Q_s (orthonormal, the same span).
+template <typename T>
+tf_status qr_rows(Handles& h, DevMem& mem, QrWork<T>& qw, T* Y, int64_t len, int k, cudaStream_t s) {
+  const int64_t cap = qr_max_elems();
+  if (len * k <= cap) return qr_inplace(h, mem, Y, len, k);
+  const int nb = (int)((len * k + cap - 1) / cap);
+  const int64_t L = (len + nb - 1) / nb;
+  if (L < k || (int64_t)nb * k * k > ((int64_t)1 << 30))
+    return api_fail(TF_EUNSUPPORTED, "QR of %lld x %d: row blocks shorter than the width", (long long)len, k);
+  if (!qw.W) {
+    TRY_CUDA(mem.get(&qw.W, (size_t)(L * k)), "cudaMalloc(QR blocks)");
+    TRY_CUDA(mem.get(&qw.W2, (size_t)(L * k)), "cudaMalloc(QR blocks)");
+    TRY_CUDA(mem.get(&qw.Rs, (size_t)nb * k * k), "cudaMalloc(QR blocks)");
+    TRY_CUDA(mem.get(&qw.tau, k), "cudaMalloc(QR)");
+    TRY_CUDA(mem.get(&qw.info, 1), "cudaMalloc(QR)");
+    int lw1 = 0, lw2 = 0;
+    TRY_LIB(geqrf_lwork(h.sol, (int)L, k, qw.W, (int)L, &lw1), "geqrf buffer");
+    TRY_LIB(orgqr_lwork(h.sol, (int)L, k, qw.W, (int)L, qw.tau, &lw2), "orgqr buffer");
+    qw.lwork = std::max(lw1, lw2);
+    TRY_CUDA(mem.get(&qw.work, qw.lwork), "cudaMalloc(QR)");
+  }
+  const size_t es = sizeof(T);
+  const int64_t ldr = (int64_t)nb * k;
+  for (int i = 0; i < nb; ++i) {
+    const int64_t r0 = i * L, Li = std::min<int64_t>(L, len - r0);
+    TRY_CUDA(cudaMemcpy2DAsync(qw.W, Li * es, Y + r0, len * es, Li * es, k, cudaMemcpyDeviceToDevice, s), "copy");
+    TRY_LIB(geqrf(h.sol, (int)Li, k, qw.W, (int)Li, qw.tau, qw.work, qw.lwork, qw.info), "geqrf");
+    k_copy_upper<T><<<grid_for((int64_t)k * k), 256, 0, s>>>(qw.Rs + (int64_t)i * k, ldr, qw.W, Li, k);
+    TRY_CUDA(cudaGetLastError(), "R copy");
+    TRY_LIB(orgqr(h.sol, (int)Li, k, qw.W, (int)Li, qw.tau, qw.work, qw.lwork, qw.info), "orgqr");
+    TRY_CUDA(cudaMemcpy2DAsync(Y + r0, len * es, qw.W, Li * es, Li * es, k, cudaMemcpyDeviceToDevice, s), "copy");
+  }
+  TRY_TF(qr_inplace(h, mem, qw.Rs, ldr, k));
+  for (int i = 0; i < nb; ++i) {
+    const int64_t r0 = i * L, Li = std::min<int64_t>(L, len - r0);
+    TRY_CUDA(cudaMemcpy2DAsync(qw.W, Li * es, Y + r0, len * es, Li * es, k, cudaMemcpyDeviceToDevice, s), "copy");
+    TRY_LIB(gemm_nn(h.blas, (int)Li, k, k, qw.W, (int)Li, qw.Rs + (int64_t)i * k, (int)ldr, qw.W2, (int)Li),
+            "gemm(Q_i Q_s)");
+    TRY_CUDA(cudaMemcpy2DAsync(Y + r0, len * es, qw.W2, Li * es, Li * es, k, cudaMemcpyDeviceToDevice, s), "copy");
+  }
   return TF_OK;
 }
 
@@ -575,16 +674,17 @@ tf_status rsvd_run(tf_op* op, const tf_irls_params* p, const void* d_obs, const 
   double* ework;
   TRY_CUDA(st.mem.get(&ework, lw), "cudaMalloc(RSVD)");
   std::vector<double> D(tp), V((size_t)tp * tp), bt(tp), w(tp);
+  QrWork<T> qn, qm;
   for (int k = 1; k <= p->kmax; ++k) {
     const double t0 = now_s();
     TRY_TF(st.begin(k));
     // Alg. 2 with one power iteration; blocks are row-major (row j = column j)
     TRY_TF(tf_rmatmat(op, tp, omega, m, Q, n, st.winv, st.wd, s));   // Y = Omega G~
-    TRY_TF(qr_rows(h, st.mem, Q, n, tp));                             // [Q, ~] = qr(Y^T)
+    TRY_TF(qr_rows(h, st.mem, qn, Q, n, tp, s));                      // [Q, ~] = qr(Y^T)
     TRY_TF(tf_matmat(op, tp, Q, n, Q1, m, st.winv, st.wd, s));        // Y = G~ Q
-    TRY_TF(qr_rows(h, st.mem, Q1, m, tp));                            // [Q1, ~] = qr(Y)
+    TRY_TF(qr_rows(h, st.mem, qm, Q1, m, tp, s));                     // [Q1, ~] = qr(Y)
     TRY_TF(tf_rmatmat(op, tp, Q1, m, Q, n, st.winv, st.wd, s));       // Y = Q1^T G~
-    TRY_TF(qr_rows(h, st.mem, Q, n, tp));                             // [Q, ~] = qr(Y^T)
+    TRY_TF(qr_rows(h, st.mem, qn, Q, n, tp, s));                      // [Q, ~] = qr(Y^T)
     TRY_TF(tf_matmat(op, tp, Q, n, Bt, m, st.winv, st.wd, s));        // B = G~ Q
     // B^T B and B^T r~ in FP64, eigen-decomposition of B^T B
     k_to_f64<T><<<grid_for((int64_t)tp * m), 256, 0, s>>>(Bd, Bt, (int64_t)tp * m);

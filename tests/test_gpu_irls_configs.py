@@ -87,6 +87,20 @@ def test_rsvd_c2_first_step(c2_rsvd, dtn):
     assert err <= TOL[dtn]
 
 
+def test_rsvd_c2_tall_skinny_qr(c2_rsvd, monkeypatch):
+    """The RSVD driver's tall-skinny QR (row blocks factored separately, their stacked R
+    factored again), which it takes when a basis block exceeds the 32-bit solver interface
+    (c4: 10^6 x 2510); forced here on c2 by a lower block bound (3 row blocks of the
+    121000 x 1260 basis), FP64 against the oracle's Householder QR step."""
+    f = c2_rsvd
+    monkeypatch.setenv("TF_QR_BLOCK_ELEMS", str(60_000_000))
+    m, r = _native(f["c"], "f64", "rsvd", f["t"], f["tp"], 1, f["omega"])
+    err = rel(m, f["m1"])
+    print(f"tf_rsvd c2 with tall-skinny QR: {err:.3e}")
+    assert abs(r.alphas[0] - f["rep1"].alphas[0]) <= 1e-10 * f["rep1"].alphas[0]
+    assert err <= TOL["f64"]
+
+
 @pytest.fixture(scope="module")
 def c3_gkb():
     c = _problem("c3", "magnetic", 50.0, 10.0, 1.4)
@@ -105,3 +119,21 @@ def test_gkb_c3_first_step(c3_gkb, dtn):
           f"{f['rep1'].alphas[0]:.6e}")
     assert abs(r.alphas[0] - f["rep1"].alphas[0]) <= (1e-10 if dtn == "f64" else 1e-4) * f["rep1"].alphas[0]
     assert err <= TOL[dtn]
+
+
+def test_rsvd_c4_fp32_matches_fp64():
+    """c4 at paper scale (250 x 200 stations, 250 x 200 x 20 cells), RSVD-IRLS with
+    k = m/20 = 2500 and oversampling 10 (t_p = 2510), one step: the FP32 driver's recovered
+    model against the FP64 driver's (itself pinned to the oracle at c1 and c2; the
+    oracle's own RSVD step at this size would take about an hour on the host)."""
+    c = _problem("c4", "gravity", 90.0, 0.0, 0.8)
+    t = c["g"].m // 20
+    tp = t + 10
+    omega = synth.gaussian_columns(c["g"].m, tp, seed=17)
+    m64, r64 = _native(c, "f64", "rsvd", t, tp, 1, omega)
+    m32, r32 = _native(c, "f32", "rsvd", t, tp, 1, omega)
+    err = rel(m32, m64)
+    print(f"tf_rsvd c4 step 1, FP32 vs FP64: {err:.3e}; alpha {r32.alphas[0]:.6e} vs {r64.alphas[0]:.6e}; "
+          f"seconds FP32 {r32.seconds[0]:.2f}, FP64 {r64.seconds[0]:.2f}")
+    assert abs(r32.alphas[0] - r64.alphas[0]) <= 1e-4 * r64.alphas[0]
+    assert err <= TOL["f32"]
