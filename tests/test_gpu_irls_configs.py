@@ -8,7 +8,10 @@
 * tf_gkb on the c3 magnetic geometry (150 x 150 stations, 150 x 150 x 20 cells) with a
   reduced t_p = 150 (the oracle keeps dense FP64 bases and runs modified Gram-Schmidt in
   Python loops, so the configuration's t_p = 2952 is beyond it), FP32 with double-float
-  re-orthogonalisation and FP64, first step against the oracle (Alg. 1).
+  re-orthogonalisation and FP64, first step against the oracle (Alg. 1);
+* at full size, where the oracle's step would take hours, the FP32 driver against the FP64
+  driver: tf_rsvd on c4 (t_p = 2510, tall-skinny QR of the 10^6-row bases) and tf_gkb on
+  c3 (t_p = 2952).
 
 Tolerances: FP64 <= 1e-11 (rounding differences of two FP64 implementations of the same
 steps, through t_p-term projections), FP32 <= 2e-5 per step against the FP64 oracle.
@@ -135,5 +138,23 @@ def test_rsvd_c4_fp32_matches_fp64():
     err = rel(m32, m64)
     print(f"tf_rsvd c4 step 1, FP32 vs FP64: {err:.3e}; alpha {r32.alphas[0]:.6e} vs {r64.alphas[0]:.6e}; "
           f"seconds FP32 {r32.seconds[0]:.2f}, FP64 {r64.seconds[0]:.2f}")
+    assert abs(r32.alphas[0] - r64.alphas[0]) <= 1e-4 * r64.alphas[0]
+    assert err <= TOL["f32"]
+
+
+def test_gkb_c3_full_fp32_matches_fp64():
+    """c3 at its full size (magnetic 150 x 150 stations, 150 x 150 x 20 cells), GKB-IRLS
+    with t = m/8 = 2812 and t_p = 1.05 t = 2952 Lanczos steps, one step: the FP32 driver
+    (double-float re-orthogonalisation) against the FP64 driver (pinned to the oracle at
+    t_p = 150 above and at c1; the oracle's dense Python Gram-Schmidt would take hours at
+    t_p = 2952)."""
+    c = _problem("c3", "magnetic", 50.0, 10.0, 1.4)
+    t = c["g"].m // 8
+    tp = int(1.05 * t)
+    m64, r64 = _native(c, "f64", "gkb", t, tp, 1)
+    m32, r32 = _native(c, "f32", "gkb", t, tp, 1)
+    err = rel(m32, m64)
+    print(f"tf_gkb c3 step 1 (t_p = {tp}), FP32 vs FP64: {err:.3e}; alpha {r32.alphas[0]:.6e} vs "
+          f"{r64.alphas[0]:.6e}; seconds FP32 {r32.seconds[0]:.2f}, FP64 {r64.seconds[0]:.2f}")
     assert abs(r32.alphas[0] - r64.alphas[0]) <= 1e-4 * r64.alphas[0]
     assert err <= TOL["f32"]
