@@ -9,6 +9,7 @@
 #include "tf_check.cuh"
 #include "tf_fft_ct.cuh"
 #include "tf_internal.h"
+#include "tf_tmem.cuh"
 
 // Transform lengths with a compile-time plan, and their radix lists (the same order
 // the host planner produces: eights first, then a four or two, then 7, 5, 3).
@@ -234,6 +235,35 @@ __global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT, 1280)) k_rows_c2r(c
 // double kernels measured no gain from it).
 template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::value;
 
+// The forward column kernel keeps its layer accumulators in tensor memory (tf_tmem.cuh)
+// in single precision with 256-thread CTAs, and then transforms MC = 2 model columns per
+// CTA: each layer's spectrum values, loaded into registers once, multiply both columns'
+// transforms, so the CTA reads them from L2 half as often.  TMEM: 128 columns per CTA, 64
+// per half of the CTA's warps, 32 per model column, 4 per slot (two complex values), one
+// slot per output of the thread's last-pass tasks.  Those tasks fill every thread, so each
+// TMEM access is warp-uniform.  The launch asks for at least kTmemSmemFloor bytes of shared
+// memory, which caps residency at 4 CTAs per SM (228 KB, 1 KB reserved per CTA), so 4 x 128
+// TMEM columns fit the SM's 512 and no allocation waits.
+// Measured (c4, 2510-column steps): the accumulator in TMEM instead of shared memory
+// 16.08 -> 15.45 ms per step.  (The adjoint's data spectrum, read once per layer, measured
+// slower from TMEM: 14.6 -> 15.1 ms at the adjoint's 80-register budget, which the TMEM
+// loads push into spills.)
+#ifndef TF_COLS_TMEM
+#define TF_COLS_TMEM 1
+#endif
+#ifndef TF_FWD_MC
+#define TF_FWD_MC 2
+#endif
+template <typename T, class P, int TB, int V, int NT> struct FwdTmem {
+  typedef ct::PassMap<P::last_r, P::last_ns, P::n, TB, V> LM;
+  static constexpr int ITA = (LM::TOTAL + NT - 1) / NT;
+  static constexpr int kColWords = 32;                       // TMEM columns per model column
+  static constexpr bool on = TF_COLS_TMEM && std::is_same<T, float>::value && NT == 256 && V == 2 &&
+                             LM::TOTAL % NT == 0 && ITA * P::last_r * 4 <= kColWords;
+  static constexpr int MC = on ? TF_FWD_MC : 1;              // model columns per CTA
+  static constexpr int kCols = 2 * MC * kColWords;           // allocation (both halves)
+};
+constexpr size_t kTmemSmemFloor = 47104;   // > 228 KB / 5 - 1 KB: at most 4 resident CTAs
 // Column stage of G x (ZHI: ny <= N/2, the layer rows fill the lower half).  In single
 // precision each thread loads the spectrum values that its last forward pass multiplies
 // at the start of every layer, into registers, so that their global-memory latency
@@ -241,20 +271,35 @@ template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::val
 template <typename T, class P, int TB, int V, int NT, bool ZHI>
 __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? kWideThreadsPerSM : kFwdThreadsPerSM<T>)) k_cols_fwd(const ColsFwd<T> a) {
   typedef typename CT<T>::C C;
+  typedef FwdTmem<T, P, TB, V, NT> FT;
   constexpr int N = P::n;
   constexpr bool kPre = kSpecPrefetch<T>;
   constexpr int RL = P::last_r, NSL = P::last_ns;
   typedef ct::PassMap<RL, NSL, N, TB, V> LM;
   constexpr int ITL = kPre ? (LM::TOTAL + NT - 1) / NT : 0;
+  // accumulator slots of the last pass (it * RL + rr) in TMEM, or [N][TB] in shared memory
+  constexpr int ITA = FT::ITA;
+  constexpr bool kTm = FT::on;
+  constexpr int MC = FT::MC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t tm_base;
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
   C* acc = buf + N * TB;
+  if constexpr (kTm)
+    if (threadIdx.x < 32) tmem::alloc(&tm_base, FT::kCols);
   for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  if constexpr (kTm) tmem::fence_before_sync();
   __syncthreads();
+  uint32_t tacc = 0;
+  if constexpr (kTm) {
+    tmem::fence_after_sync();
+    tacc = tmem::lane_addr(tm_base, (threadIdx.x >> 7) * (FT::kCols / 2));
+  }
   const int k0 = blockIdx.x * TB;
   const int nh = a.nh, hs = a.hs, ny = a.ny, sy = a.sy;
-  const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
+  const int col0 = blockIdx.y * MC;
+  const int mc = MC > 1 && a.ncols - col0 < MC ? a.ncols - col0 : MC;   // the CTA's columns
   const int z_ext = a.nz * ny * hs, g_ext = a.nz * N * hs, s_ext = sy * hs;
   const C* spec = a.spec;
   C gpre[kPre ? ITL * RL : 1][V];
@@ -274,45 +319,94 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
       }
     }
     const bool first_layer = (r == 0);
-    // Row-transformed layers as aligned vectors without a padding mask: the workspace is
-    // zeroed when allocated, the row kernels never write its padding, and the column
-    // kernels write zeros there (their padded sequences have zero inputs).  A masked load
-    // measured much slower here (the mask's select waits for the load).
-    auto load = [=](int idx, int b0, C* o) {
-      const int k1 = k0 + b0;
-      const int e = zoff + idx * hs + k1;
-      ld_row_vec<V, false>(z + e, k1, nh, idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e + V - 1, z_ext), o);
-    };
-    auto mac = [&](int idx, int b0, const C* v, int slot) {
-      C cur[V];
-      const bool acc_ok = TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB);
-      if (!first_layer && acc_ok) Vec<V, C>::ld(acc + idx * TB + b0, cur);
-      C gv[V];
-      if constexpr (!kPre) {
+    for (int c = 0; c < MC; ++c) {
+      if (c >= mc) break;
+      const C* z = a.z + (int64_t)(col0 + c) * a.z_ld;
+      const uint32_t tcol = tacc + c * FT::kColWords;
+      // Row-transformed layers as aligned vectors without a padding mask: the workspace is
+      // zeroed when allocated, the row kernels never write its padding, and the column
+      // kernels write zeros there (their padded sequences have zero inputs).  A masked load
+      // measured much slower here (the mask's select waits for the load).
+      auto load = [=](int idx, int b0, C* o) {
         const int k1 = k0 + b0;
-        const int e = goff + idx * hs + k1;
-        ld_row_vec<V, false>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteFwdSpec, e + V - 1, g_ext), gv);
-      }
+        const int e = zoff + idx * hs + k1;
+        ld_row_vec<V, false>(z + e, k1, nh, idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e + V - 1, z_ext), o);
+      };
+      auto mac = [&](int idx, int b0, const C* v, int slot) {
+        C cur[V];
+        const bool acc_ok = TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB);
+        if constexpr (kTm) {
+          if (!first_layer) {
+            float f[4];
+            tmem::ld4(tcol + slot * 4, f);
+            cur[0] = mk<C>(f[0], f[1]);
+            cur[1] = mk<C>(f[2], f[3]);
+          }
+        } else {
+          if (!first_layer && acc_ok) Vec<V, C>::ld(acc + idx * TB + b0, cur);
+        }
+        C gv[V];
+        if constexpr (!kPre) {
+          const int k1 = k0 + b0;
+          const int e = goff + idx * hs + k1;
+          ld_row_vec<V, false>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteFwdSpec, e + V - 1, g_ext), gv);
+        }
 #pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const C g = kPre ? gpre[slot][q] : gv[q];
-        const C p = cmul(g, v[q]);
-        cur[q] = first_layer ? p : cadd(cur[q], p);
-      }
-      if (acc_ok) Vec<V, C>::st(acc + idx * TB + b0, cur);
-    };
-    P::template run<TB, V, NT, false, ZHI>(tw, buf, load, mac);
+        for (int q = 0; q < V; ++q) {
+          const C g = kPre ? gpre[slot][q] : gv[q];
+          const C p = cmul(g, v[q]);
+          cur[q] = first_layer ? p : cadd(cur[q], p);
+        }
+        if constexpr (kTm) {
+          const float f[4] = {cur[0].x, cur[0].y, cur[1].x, cur[1].y};
+          tmem::st4(tcol + slot * 4, f);
+        } else {
+          if (acc_ok) Vec<V, C>::st(acc + idx * TB + b0, cur);
+        }
+      };
+      P::template run<TB, V, NT, false, ZHI>(tw, buf, load, mac);
+      if constexpr (kTm) tmem::wait_st();
+    }
   }
-  C* s = a.s + (int64_t)blockIdx.y * a.s_ld;
-  auto lacc = [=](int idx, int b0, C* o) {
-    if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::ld(acc + idx * TB + b0, o);
-  };
-  auto store = [=](int idx, int b0, const C* v, int) {
-    const int j = idx - (ny - 1), k1 = k0 + b0;
-    if (j < 0 || j >= sy || k1 >= nh) return;
-    if (TF_IN(kSiteFwdS, j * hs + k1 + V - 1, s_ext)) Vec<V, C>::st(s + j * hs + k1, v);
-  };
-  P::template run<TB, V, NT, true>(tw, buf, lacc, store);
+  for (int c = 0; c < MC; ++c) {
+    if (c >= mc) break;
+    C* s = a.s + (int64_t)(col0 + c) * a.s_ld;
+    auto lacc = [=](int idx, int b0, C* o) {
+      if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::ld(acc + idx * TB + b0, o);
+    };
+    auto store = [=](int idx, int b0, const C* v, int) {
+      const int j = idx - (ny - 1), k1 = k0 + b0;
+      if (j < 0 || j >= sy || k1 >= nh) return;
+      if (TF_IN(kSiteFwdS, j * hs + k1 + V - 1, s_ext)) Vec<V, C>::st(s + j * hs + k1, v);
+    };
+    if constexpr (kTm) {
+      // the accumulator from TMEM into the working buffer, in the inverse's input order
+      const uint32_t tcol = tacc + c * FT::kColWords;
+#pragma unroll
+      for (int it = 0; it < ITA; ++it) {
+        int b0;
+        const int base = LM::first_idx(threadIdx.x + it * NT, b0);
+#pragma unroll
+        for (int rr = 0; rr < RL; ++rr) {
+          float f[4];
+          tmem::ld4(tcol + (it * RL + rr) * 4, f);
+          const C v[2] = {mk<C>(f[0], f[1]), mk<C>(f[2], f[3])};
+          const int e = ct::at<C, TB, P::first_r>(base + rr * NSL, b0);
+          if (TF_IN(kSiteSmem + 2, e + V - 1, N * TB)) Vec<V, C>::st(buf + e, v);
+        }
+      }
+      tmem::fence_before_sync();
+      __syncthreads();
+      if (c == mc - 1 && threadIdx.x < 32) {
+        tmem::fence_after_sync();
+        tmem::dealloc(tm_base, FT::kCols);
+      }
+      const ct::Buf<C, TB, V, P::first_r> b{buf, N * TB};
+      P::template run<TB, V, NT, true>(tw, buf, b, store);
+    } else {
+      P::template run<TB, V, NT, true>(tw, buf, lacc, store);
+    }
+  }
 }
 
 // Column stage of G^T y: forward transform of the data columns into shared memory, then
@@ -435,11 +529,15 @@ cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
 template <typename T, class P>
 cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
   typedef ColTiles<T, P> TL;
+  typedef FwdTmem<T, P, TL::TB, TL::V, TL::NT> FT;
   const bool zhi = P::can_zero_hi && a.ny <= P::n / 2;
-  const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
-  const dim3 grid(cdiv(a.nh, TL::TB), ncols);
-  if (zhi) return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, true>>(a, grid, TL::NT, sm, s);
-  return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, false>>(a, grid, TL::NT, sm, s);
+  size_t sm = (size_t)(twpad(P::n - 1) + (FT::on ? 1 : 2) * P::n * TL::TB) * sizeof(typename CT<T>::C);
+  if (FT::on && sm < kTmemSmemFloor) sm = kTmemSmemFloor;   // the residency cap of FwdTmem
+  const dim3 grid(cdiv(a.nh, TL::TB), cdiv(ncols, FT::MC));
+  ColsFwd<T> ac = a;
+  ac.ncols = ncols;
+  if (zhi) return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, true>>(ac, grid, TL::NT, sm, s);
+  return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, false>>(ac, grid, TL::NT, sm, s);
 }
 template <typename T, class P>
 cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {

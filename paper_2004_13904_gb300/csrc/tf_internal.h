@@ -37,6 +37,7 @@ template <typename T> struct ColsFwd {
   typename CT<T>::C* s; int64_t s_ld;             // [sy][hs] per column
   int nh, hs, ny, sy, nz;
   FftPlan plan; const typename CT<T>::C* tw;
+  int ncols;                                      // columns of the launch (set by the launcher)
 };
 
 // Column stage of G^T y: FFT along y of the data rows placed at [ny-1, ny-1+sy), then

@@ -123,3 +123,34 @@ def test_menus_parsed():
     rows, cols = _menu("TF_CT_MENU"), _menu("TF_CT_MENU_COLS_F32")
     assert (224, 8, 4, 7) in rows and (224, 16, 14) in cols
     assert [e[0] for e in rows] == [e[0] for e in cols]
+
+
+def test_forward_accumulator_tmem_budget():
+    """cols_fwd keeps the layer accumulators of MC model columns in tensor memory for
+    single-precision plans on 256-thread CTAs: the last pass's slots (iterations x last
+    radix x 4 words) fit the 32 columns given to each model column in each half of the
+    CTA's warps, the last pass gives every thread a task (every TMEM access warp-uniform),
+    and the shared-memory request lets at most 4 CTAs reside on an SM (228 KB, 1 KB
+    reserved per CTA), whose allocations then fit the SM's 512 columns (none waits)."""
+    text = open(HDR).read()
+    col_words = int(re.search(r"kColWords = (\d+);", text).group(1))
+    mc = int(re.search(r"#define TF_FWD_MC (\d+)", text).group(1))
+    floor = int(re.search(r"constexpr size_t kTmemSmemFloor = (\d+);", text).group(1))
+    alloc = 2 * mc * col_words
+    assert alloc in (32, 64, 128, 256, 512)          # a power of two, at least 32
+    used = 0
+    for N, *radices in _menu("TF_CT_MENU_COLS_F32"):
+        TB, V, NT = _tiles(N, radices, "f32")
+        if NT != 256:
+            continue
+        R = radices[-1]
+        total = (N // R) * (TB // V)
+        iters = (total + NT - 1) // NT
+        assert total % NT == 0, (N, radices)
+        assert iters * R * 4 <= col_words, (N, radices)
+        tw = (N - 1 + 1) & ~1
+        smem = max((tw + N * TB) * 8, floor)
+        resident = min(233472 // (smem + 1024), 2048 // NT)
+        assert resident * alloc <= 512, (N, resident)
+        used += 1
+    assert used >= 3          # 320, 448 and 512
