@@ -78,6 +78,10 @@ template <typename T> constexpr int kFwdThreadsPerSM = 512;
 constexpr int kWideThreadsPerSM = 384;
 // the adjoint at n >= 448 (256 threads per CTA) measured fastest with a tighter budget
 template <typename T, int N> constexpr int kAdjThreadsPerSM = N >= 448 ? 768 : 640;
+// Buffer positions from per-task bases (Buf's STEP) in the forward column kernel only: c4
+// cols_fwd 14.99 -> 13.71 ms per 2510-column step, while the adjoint measured slower with
+// them (14.56 -> 16.3 ms at its 80-register budget, 16.0 ms at 128 registers).
+constexpr bool kAdjStep = false;
 
 // Visits every (element index n < E, pair group q < TP) once.  When E fills at least 4/5
 // of the CTA's threads, each thread takes whole element indices and loops over the pair
@@ -280,6 +284,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   // accumulator slots of the last pass (it * RL + rr) in TMEM, or [N][TB] in shared memory
   constexpr int ITA = FT::ITA;
   constexpr bool kTm = FT::on;
+  static_assert(!kTm || (kPre && V == 2), "TMEM accumulators: register-staged spectrum, pairs");
   constexpr int MC = FT::MC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t tm_base;
@@ -295,6 +300,13 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   if constexpr (kTm) {
     tmem::fence_after_sync();
     tacc = tmem::lane_addr(tm_base, (threadIdx.x >> 7) * (FT::kCols / 2));
+    // zero accumulators: every layer, the first included, is then one multiply-add
+    const float z4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < MC; ++c)
+#pragma unroll
+      for (int sl = 0; sl < ITA * RL; ++sl) tmem::st4(tacc + c * FT::kColWords + sl * 4, z4);
+    tmem::wait_st();
   }
   const int k0 = blockIdx.x * TB;
   const int nh = a.nh, hs = a.hs, ny = a.ny, sy = a.sy;
@@ -333,38 +345,39 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
         ld_row_vec<V, false>(z + e, k1, nh, idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e + V - 1, z_ext), o);
       };
       auto mac = [&](int idx, int b0, const C* v, int slot) {
-        C cur[V];
-        const bool acc_ok = TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB);
         if constexpr (kTm) {
-          if (!first_layer) {
-            float f[4];
-            tmem::ld4(tcol + slot * 4, f);
-            cur[0] = mk<C>(f[0], f[1]);
-            cur[1] = mk<C>(f[2], f[3]);
-          }
-        } else {
-          if (!first_layer && acc_ok) Vec<V, C>::ld(acc + idx * TB + b0, cur);
-        }
-        C gv[V];
-        if constexpr (!kPre) {
-          const int k1 = k0 + b0;
-          const int e = goff + idx * hs + k1;
-          ld_row_vec<V, false>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteFwdSpec, e + V - 1, g_ext), gv);
-        }
+          // acc += g v as four fused multiply-adds per complex value (accumulators zeroed)
+          float f[4];
+          tmem::ld4(tcol + slot * 4, f);
 #pragma unroll
-        for (int q = 0; q < V; ++q) {
-          const C g = kPre ? gpre[slot][q] : gv[q];
-          const C p = cmul(g, v[q]);
-          cur[q] = first_layer ? p : cadd(cur[q], p);
-        }
-        if constexpr (kTm) {
-          const float f[4] = {cur[0].x, cur[0].y, cur[1].x, cur[1].y};
+          for (int q = 0; q < 2; ++q) {
+            const C g = gpre[slot][q];
+            f[2 * q] = fmaf(g.x, v[q].x, f[2 * q]);
+            f[2 * q] = fmaf(-g.y, v[q].y, f[2 * q]);
+            f[2 * q + 1] = fmaf(g.x, v[q].y, f[2 * q + 1]);
+            f[2 * q + 1] = fmaf(g.y, v[q].x, f[2 * q + 1]);
+          }
           tmem::st4(tcol + slot * 4, f);
         } else {
+          C cur[V];
+          const bool acc_ok = TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB);
+          if (!first_layer && acc_ok) Vec<V, C>::ld(acc + idx * TB + b0, cur);
+          C gv[V];
+          if constexpr (!kPre) {
+            const int k1 = k0 + b0;
+            const int e = goff + idx * hs + k1;
+            ld_row_vec<V, false>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteFwdSpec, e + V - 1, g_ext), gv);
+          }
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            const C g = kPre ? gpre[slot][q] : gv[q];
+            const C p = cmul(g, v[q]);
+            cur[q] = first_layer ? p : cadd(cur[q], p);
+          }
           if (acc_ok) Vec<V, C>::st(acc + idx * TB + b0, cur);
         }
       };
-      P::template run<TB, V, NT, false, ZHI>(tw, buf, load, mac);
+      P::template run<TB, V, NT, false, ZHI, true>(tw, buf, load, mac);
       if constexpr (kTm) tmem::wait_st();
     }
   }
@@ -401,10 +414,10 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
         tmem::fence_after_sync();
         tmem::dealloc(tm_base, FT::kCols);
       }
-      const ct::Buf<C, TB, V, P::first_r> b{buf, N * TB};
-      P::template run<TB, V, NT, true>(tw, buf, b, store);
+      const ct::Buf<C, TB, V, P::first_r, true> b{buf, N * TB};
+      P::template run<TB, V, NT, true, false, true>(tw, buf, b, store);
     } else {
-      P::template run<TB, V, NT, true>(tw, buf, lacc, store);
+      P::template run<TB, V, NT, true, false, true>(tw, buf, lacc, store);
     }
   }
 }
@@ -433,7 +446,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   auto sacc = [=](int idx, int b0, const C* v, int) {
     if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::st(acc + idx * TB + b0, v);
   };
-  P::template run<TB, V, NT, false>(tw, buf, load, sacc);
+  P::template run<TB, V, NT, false, false, kAdjStep>(tw, buf, load, sacc);
   C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
   const C* spec = a.spec;
   for (int r = 0; r < a.nz; ++r) {
@@ -453,7 +466,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
       const int e = uoff + idx * hs + k1;
       if (TF_IN(kSiteAdjU, e + V - 1, u_ext)) Vec<V, C>::st(u + e, v);
     };
-    P::template run<TB, V, NT, true>(tw, buf, prod, store);
+    P::template run<TB, V, NT, true, false, kAdjStep>(tw, buf, prod, store);
   }
 }
 

@@ -65,10 +65,33 @@ template <typename C, int TB, int S = 8> __host__ __device__ constexpr int row_o
   constexpr int q = TB * (int)sizeof(C) == 64 ? 2 : TB * (int)sizeof(C) == 32 ? 4 : 1;
   return q > 1 ? idx ^ ((idx / S) & (q - 1)) : idx;
 }
-template <typename C, int TB, int S = 8> __host__ __device__ __forceinline__ int at(int idx, int b) {
+template <typename C, int TB, int S = 8> __host__ __device__ constexpr int at(int idx, int b) {
   const int row = row_of<C, TB, S>(idx);
   return row * TB + (b ^ swz<C, TB>(row));
 }
+
+// How the R positions idx = f + r st of one task (f its first index) move in the buffer,
+// checked over every task of a pass at compile time: 1 when at(f + r st, b) = at(f, b) +
+// r st TB for all r and b (the addresses are one base plus constant offsets), 2 when that
+// holds separately for even r (base at(f)) and odd r (base at(f + st)), 0 otherwise.
+// Loads of a pass have f = j, st = NB; its stores f = (j - j mod Ns) R + j mod Ns, st = Ns.
+template <typename C, int TB, int S>
+constexpr int step_mode(int NB, int R, int Ns, bool store) {
+  const int st = store ? Ns : NB;
+  bool one = true, two = true;
+  for (int j = 0; j < NB && (one || two); ++j) {
+    const int f = store ? (j - j % Ns) * R + j % Ns : j;
+    for (int b = 0; b < TB; ++b)
+      for (int r = 0; r < R; ++r) {
+        const int e = at<C, TB, S>(f + r * st, b);
+        if (e != at<C, TB, S>(f, b) + r * st * TB) one = false;
+        if (e != at<C, TB, S>(f + (r & 1) * st, b) + (r - (r & 1)) * st * TB) two = false;
+      }
+  }
+  return one ? 1 : two ? 2 : 0;
+}
+template <typename C, int TB, int S, int NB, int R, int Ns, bool STORE>
+constexpr int kStepMode = step_mode<C, TB, S>(NB, R, Ns, STORE);
 
 // at(idx, b) for a fixed idx and varying even b: the row's base and swizzle computed once.
 template <typename C, int TB, int S = 8> struct RowAt {
@@ -82,8 +105,12 @@ template <typename C, int TB, int S = 8> struct RowAt {
 };
 
 // The working buffer: [N][TB] complex, sequence index fastest (swizzled).
-template <typename C, int TB, int V, int S = 8> struct Buf {
-  static constexpr bool kIsBuf = true;
+// STEP: a pass whose loads / stores go through this buffer computes each task's positions
+// from one or two bases (step_mode) instead of per element; kernels with a tight register
+// budget (the row kernels) keep the per-element form, which needs fewer live registers.
+template <typename C, int TB, int V, int S = 8, bool STEP = false> struct Buf {
+  static constexpr bool kIsBuf = true, kStep = STEP;
+  static constexpr int kTB = TB, kS = S;
   C* p;
   int ext;  // elements of the buffer (checked builds test every access against it)
   __device__ __forceinline__ void operator()(int idx, int b0, C* o) const {
@@ -98,6 +125,20 @@ template <typename C, int TB, int V, int S = 8> struct Buf {
 
 template <class T, class = void> struct IsBuf : std::false_type {};
 template <class T> struct IsBuf<T, std::void_t<decltype(T::kIsBuf)>> : std::true_type {};
+
+// step_mode of a pass's buffer loads / stores (0 for other loaders and storers).
+template <class L, typename C, int NB, int R, bool = IsBuf<L>::value> struct LoadMode {
+  static constexpr int value = 0;
+};
+template <class L, typename C, int NB, int R> struct LoadMode<L, C, NB, R, true> {
+  static constexpr int value = L::kStep ? kStepMode<C, L::kTB, L::kS, NB, R, 1, false> : 0;
+};
+template <class S, typename C, int NB, int R, int Ns, bool = IsBuf<S>::value> struct StoreMode {
+  static constexpr int value = 0;
+};
+template <class S, typename C, int NB, int R, int Ns> struct StoreMode<S, C, NB, R, Ns, true> {
+  static constexpr int value = S::kStep ? kStepMode<C, S::kTB, S::kS, NB, R, Ns, true> : 0;
+};
 
 // The task -> (output index, sequence) mapping of a pass, as the pass computes it: task
 // u writes first_idx(u) + r * Ns, r < R, for sequences b0 .. b0 + V - 1.
@@ -155,12 +196,21 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
     const int u = threadIdx.x + it * NT;
     if (TOTAL % NT == 0 || u < TOTAL) {
       const int j = u / G, b0 = (u % G) * V;
+      constexpr int LMODE = LoadMode<L, C, NB, R>::value;
+      int e0 = 0, e1 = 0;
+      if constexpr (LMODE > 0) {
+        e0 = at<C, TB, L::kS>(j, b0);
+        if constexpr (LMODE == 2) e1 = at<C, TB, L::kS>(j + NB, b0);
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         C t[V];
         if (ZHI && r >= R / 2) {
 #pragma unroll
           for (int q = 0; q < V; ++q) t[q] = mk<C>(0, 0);
+        } else if constexpr (LMODE > 0) {
+          const int e = (LMODE == 2 && (r & 1)) ? e1 + (r - 1) * NB * TB : e0 + r * NB * TB;
+          if (TF_IN(kSiteSmem, e + V - 1, ld.ext) && TF_IN(kSiteSmem, e, ld.ext)) Vec<V, C>::ld(ld.p + e, t);
         } else {
           ld(j + r * NB, b0, t);
         }
@@ -193,12 +243,23 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
     if (TOTAL % NT == 0 || u < TOTAL) {
       int b0;
       const int base = PassMap<R, Ns, N, TB, V>::first_idx(u, b0);
+      constexpr int SMODE = StoreMode<S, C, NB, R, Ns>::value;
+      int e0 = 0, e1 = 0;
+      if constexpr (SMODE > 0) {
+        e0 = at<C, TB, S::kS>(base, b0);
+        if constexpr (SMODE == 2) e1 = at<C, TB, S::kS>(base + Ns, b0);
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         C t[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) t[q] = v[it][q][r];
-        st(base + r * Ns, b0, t, it * R + r);
+        if constexpr (SMODE > 0) {
+          const int e = (SMODE == 2 && (r & 1)) ? e1 + (r - 1) * Ns * TB : e0 + r * Ns * TB;
+          if (TF_IN(kSiteSmem, e + V - 1, st.ext) && TF_IN(kSiteSmem, e, st.ext)) Vec<V, C>::st(st.p + e, t);
+        } else {
+          st(base + r * Ns, b0, t, it * R + r);
+        }
       }
     }
   }
@@ -209,16 +270,16 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
 // `last`, the others use the shared buffer.  Twiddle layout as in FftPlan.
 template <int N, int Ns, int TwOff, int... Rs> struct Run;
 template <int N, int Ns, int TwOff, int R, int... Rest> struct Run<N, Ns, TwOff, R, Rest...> {
-  template <int TB, int V, int NT, bool INV, bool FIRST, bool ZHI, int S, typename C, class L0, class SL>
+  template <int TB, int V, int NT, bool INV, bool FIRST, bool ZHI, int S, bool STEP, typename C, class L0, class SL>
   static __device__ __forceinline__ void go(const C* tw, C* buf, const L0& first, const SL& last) {
     constexpr bool LAST = sizeof...(Rest) == 0;
-    const Buf<C, TB, V, S> b{buf, N * TB};
+    const Buf<C, TB, V, S, STEP> b{buf, N * TB};
     if constexpr (FIRST && LAST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, last);
     else if constexpr (FIRST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, b);
     else if constexpr (LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, last);
     else pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, b);
     if constexpr (!LAST)
-      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false, false, S>(
+      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false, false, S, STEP>(
           tw, buf, first, last);
   }
 };
@@ -240,9 +301,10 @@ template <int N, int... Rs> struct Plan {
   // first radix is even.
   static constexpr int first_r = FirstOf<Rs...>::r;        // radix of the first pass
   static constexpr bool can_zero_hi = first_r % 2 == 0;
-  template <int TB, int V, int NT, bool INV, bool ZHI = false, typename C, class L0, class SL>
+  template <int TB, int V, int NT, bool INV, bool ZHI = false, bool STEP = false, typename C, class L0, class SL>
   static __device__ __forceinline__ void run(const C* tw, C* buf, const L0& first, const SL& last) {
-    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r>(tw, buf, first, last);
+    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r, STEP>(tw, buf, first,
+                                                                                              last);
   }
 };
 
