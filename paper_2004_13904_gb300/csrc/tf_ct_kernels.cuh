@@ -80,8 +80,12 @@ constexpr int kWideThreadsPerSM = 384;
 template <typename T, int N> constexpr int kAdjThreadsPerSM = N >= 448 ? 768 : 640;
 // Buffer positions from per-task bases (Buf's STEP) in the forward column kernel only: c4
 // cols_fwd 14.99 -> 13.71 ms per 2510-column step, while the adjoint measured slower with
-// them (14.56 -> 16.3 ms at its 80-register budget, 16.0 ms at 128 registers).
-constexpr bool kAdjStep = false;
+// them for its loads (14.56 -> 16.3 ms at its 80-register budget, 16.0 ms at 128
+// registers) and no faster for its stores alone.
+constexpr int kAdjStep = 0;
+// The row kernels keep per-element positions too (with bases: rows_r2c 7.96 -> 8.8 ms, and
+// at a 48-register budget 8.9 ms; rows_c2r 8.41 -> 8.62 ms).
+constexpr int kRowsStep = 0;
 
 // Visits every (element index n < E, pair group q < TP) once.  When E fills at least 4/5
 // of the CTA's threads, each thread takes whole element indices and loops over the pair
@@ -150,8 +154,8 @@ __global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT, 1536)) k_rows_r2c(c
     if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::st(buf + p, v);
   });
   __syncthreads();
-  const ct::Buf<C, TB, V, P::first_r> b{buf, N * TB};
-  P::template run<TB, V, NT, false, ZHI>(tw, buf, b, b);
+  const ct::Buf<C, TB, V, P::first_r, kRowsStep> b{buf, N * TB};
+  P::template run<TB, V, NT, false, ZHI, kRowsStep>(tw, buf, b, b);
   C* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int hs = a.hs, dst_ext = nrows * hs;
   visit_pairs<NT, TP>(NH, [&](int k, int q) {
@@ -212,8 +216,8 @@ __global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT, 1280)) k_rows_c2r(c
     }
   });
   __syncthreads();
-  const ct::Buf<C, TB, V, P::first_r> b{buf, N * TB};
-  P::template run<TB, V, NT, true>(tw, buf, b, b);
+  const ct::Buf<C, TB, V, P::first_r, kRowsStep> b{buf, N * TB};
+  P::template run<TB, V, NT, true, false, kRowsStep>(tw, buf, b, b);
   T* dst = a.dst + (int64_t)blockIdx.y * a.dst_ld;
   const int L = a.out_len, off = a.seq_off;
   const int dst_ext = nrows * L;
@@ -258,6 +262,9 @@ template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::val
 #ifndef TF_FWD_MC
 #define TF_FWD_MC 2
 #endif
+#ifndef TF_FWD_PP
+#define TF_FWD_PP 1   // measured: c4 cols_fwd 13.72 -> 12.66 ms per step with the two buffers
+#endif
 template <typename T, class P, int TB, int V, int NT> struct FwdTmem {
   typedef ct::PassMap<P::last_r, P::last_ns, P::n, TB, V> LM;
   static constexpr int ITA = (LM::TOTAL + NT - 1) / NT;
@@ -265,6 +272,8 @@ template <typename T, class P, int TB, int V, int NT> struct FwdTmem {
   static constexpr bool on = TF_COLS_TMEM && std::is_same<T, float>::value && NT == 256 && V == 2 &&
                              LM::TOTAL % NT == 0 && ITA * P::last_r * 4 <= kColWords;
   static constexpr int MC = on ? TF_FWD_MC : 1;              // model columns per CTA
+  static constexpr bool pp = on && TF_FWD_PP;                // passes alternate two buffers
+  static constexpr int nbuf = on && !pp ? 1 : 2;             // shared-memory buffers of N x TB
   static constexpr int kCols = 2 * MC * kColWords;           // allocation (both halves)
 };
 constexpr size_t kTmemSmemFloor = 47104;   // > 228 KB / 5 - 1 KB: at most 4 resident CTAs
@@ -286,6 +295,10 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   constexpr bool kTm = FT::on;
   static_assert(!kTm || (kPre && V == 2), "TMEM accumulators: register-staged spectrum, pairs");
   constexpr int MC = FT::MC;
+  // with the accumulators in TMEM, the second buffer pairs with the first so that
+  // consecutive passes alternate between them (Plan::run2: no barrier inside a pass)
+  constexpr bool kPP = FT::pp;
+  static_assert(!kPP || FT::nbuf == 2, "ping-pong needs the second buffer");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t tm_base;
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -377,7 +390,8 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
           if (acc_ok) Vec<V, C>::st(acc + idx * TB + b0, cur);
         }
       };
-      P::template run<TB, V, NT, false, ZHI, true>(tw, buf, load, mac);
+      if constexpr (kPP) P::template run2<TB, V, NT, false, ZHI, 3>(tw, buf, acc, load, mac);
+      else P::template run<TB, V, NT, false, ZHI, 3>(tw, buf, load, mac);
       if constexpr (kTm) tmem::wait_st();
     }
   }
@@ -405,7 +419,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
           tmem::ld4(tcol + (it * RL + rr) * 4, f);
           const C v[2] = {mk<C>(f[0], f[1]), mk<C>(f[2], f[3])};
           const int e = ct::at<C, TB, P::first_r>(base + rr * NSL, b0);
-          if (TF_IN(kSiteSmem + 2, e + V - 1, N * TB)) Vec<V, C>::st(buf + e, v);
+          if (TF_IN(kSiteSmem + 2, e + V - 1, N * TB)) Vec<V, C>::st((kPP ? acc : buf) + e, v);
         }
       }
       tmem::fence_before_sync();
@@ -414,10 +428,15 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
         tmem::fence_after_sync();
         tmem::dealloc(tm_base, FT::kCols);
       }
-      const ct::Buf<C, TB, V, P::first_r, true> b{buf, N * TB};
-      P::template run<TB, V, NT, true, false, true>(tw, buf, b, store);
+      if constexpr (kPP) {
+        const ct::Buf<C, TB, V, P::first_r, 3, 1> b{acc, N * TB};
+        P::template run2<TB, V, NT, true, false, 3>(tw, buf, acc, b, store);
+      } else {
+        const ct::Buf<C, TB, V, P::first_r, 3> b{buf, N * TB};
+        P::template run<TB, V, NT, true, false, 3>(tw, buf, b, store);
+      }
     } else {
-      P::template run<TB, V, NT, true, false, true>(tw, buf, lacc, store);
+      P::template run<TB, V, NT, true, false, 3>(tw, buf, lacc, store);
     }
   }
 }
@@ -544,7 +563,7 @@ cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
   typedef ColTiles<T, P> TL;
   typedef FwdTmem<T, P, TL::TB, TL::V, TL::NT> FT;
   const bool zhi = P::can_zero_hi && a.ny <= P::n / 2;
-  size_t sm = (size_t)(twpad(P::n - 1) + (FT::on ? 1 : 2) * P::n * TL::TB) * sizeof(typename CT<T>::C);
+  size_t sm = (size_t)(twpad(P::n - 1) + FT::nbuf * P::n * TL::TB) * sizeof(typename CT<T>::C);
   if (FT::on && sm < kTmemSmemFloor) sm = kTmemSmemFloor;   // the residency cap of FwdTmem
   const dim3 grid(cdiv(a.nh, TL::TB), cdiv(ncols, FT::MC));
   ColsFwd<T> ac = a;

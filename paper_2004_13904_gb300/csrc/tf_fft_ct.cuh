@@ -75,6 +75,8 @@ template <typename C, int TB, int S = 8> __host__ __device__ constexpr int at(in
 // r st TB for all r and b (the addresses are one base plus constant offsets), 2 when that
 // holds separately for even r (base at(f)) and odd r (base at(f + st)), 0 otherwise.
 // Loads of a pass have f = j, st = NB; its stores f = (j - j mod Ns) R + j mod Ns, st = Ns.
+// (A third form for the first pass's stores, two bases plus a per-element XOR of the
+// sequence index, measured no faster at n = 448 and slower for the radix-16 first pass.)
 template <typename C, int TB, int S>
 constexpr int step_mode(int NB, int R, int Ns, bool store) {
   const int st = store ? Ns : NB;
@@ -93,6 +95,7 @@ constexpr int step_mode(int NB, int R, int Ns, bool store) {
 template <typename C, int TB, int S, int NB, int R, int Ns, bool STORE>
 constexpr int kStepMode = step_mode<C, TB, S>(NB, R, Ns, STORE);
 
+
 // at(idx, b) for a fixed idx and varying even b: the row's base and swizzle computed once.
 template <typename C, int TB, int S = 8> struct RowAt {
   int base, sw;
@@ -105,11 +108,15 @@ template <typename C, int TB, int S = 8> struct RowAt {
 };
 
 // The working buffer: [N][TB] complex, sequence index fastest (swizzled).
-// STEP: a pass whose loads / stores go through this buffer computes each task's positions
-// from one or two bases (step_mode) instead of per element; kernels with a tight register
-// budget (the row kernels) keep the per-element form, which needs fewer live registers.
-template <typename C, int TB, int V, int S = 8, bool STEP = false> struct Buf {
-  static constexpr bool kIsBuf = true, kStep = STEP;
+// STEP (bit 0 loads, bit 1 stores): a pass whose loads / stores go through this buffer
+// computes each task's positions from one or two bases (step_mode) instead of per element;
+// kernels with a tight register budget keep the per-element form, which needs fewer live
+// registers.
+// SLOT names the buffer: a pass whose loads and stores go through Buf's of the same slot
+// works in place (a barrier between its loads and its stores).
+template <typename C, int TB, int V, int S = 8, int STEP = 0, int SLOT = 0> struct Buf {
+  static constexpr bool kIsBuf = true;
+  static constexpr int kStep = STEP, kSlot = SLOT;
   static constexpr int kTB = TB, kS = S;
   C* p;
   int ext;  // elements of the buffer (checked builds test every access against it)
@@ -125,19 +132,21 @@ template <typename C, int TB, int V, int S = 8, bool STEP = false> struct Buf {
 
 template <class T, class = void> struct IsBuf : std::false_type {};
 template <class T> struct IsBuf<T, std::void_t<decltype(T::kIsBuf)>> : std::true_type {};
+template <class L, class S, bool = IsBuf<L>::value && IsBuf<S>::value> struct SameBuf : std::false_type {};
+template <class L, class S> struct SameBuf<L, S, true> : std::bool_constant<L::kSlot == S::kSlot> {};
 
 // step_mode of a pass's buffer loads / stores (0 for other loaders and storers).
 template <class L, typename C, int NB, int R, bool = IsBuf<L>::value> struct LoadMode {
   static constexpr int value = 0;
 };
 template <class L, typename C, int NB, int R> struct LoadMode<L, C, NB, R, true> {
-  static constexpr int value = L::kStep ? kStepMode<C, L::kTB, L::kS, NB, R, 1, false> : 0;
+  static constexpr int value = (L::kStep & 1) ? kStepMode<C, L::kTB, L::kS, NB, R, 1, false> : 0;
 };
 template <class S, typename C, int NB, int R, int Ns, bool = IsBuf<S>::value> struct StoreMode {
   static constexpr int value = 0;
 };
 template <class S, typename C, int NB, int R, int Ns> struct StoreMode<S, C, NB, R, Ns, true> {
-  static constexpr int value = S::kStep ? kStepMode<C, S::kTB, S::kS, NB, R, Ns, true> : 0;
+  static constexpr int value = (S::kStep & 2) ? kStepMode<C, S::kTB, S::kS, NB, R, Ns, true> : 0;
 };
 
 // The task -> (output index, sequence) mapping of a pass, as the pass computes it: task
@@ -189,7 +198,7 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
   constexpr int G = TB / V;
   constexpr int TOTAL = NB * G;
   constexpr int ITER = (TOTAL + NT - 1) / NT;
-  constexpr bool kInPlace = IsBuf<L>::value && IsBuf<S>::value;
+  constexpr bool kInPlace = SameBuf<L, S>::value;
   C v[ITER][V][R];
 #pragma unroll
   for (int it = 0; it < ITER; ++it) {
@@ -269,18 +278,24 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
 // Passes of a radix list; pass 0 loads through `first`, the last pass stores through
 // `last`, the others use the shared buffer.  Twiddle layout as in FftPlan.
 template <int N, int Ns, int TwOff, int... Rs> struct Run;
+// Pass K of a plan stores into buffer slot (PP ? K mod 2 : 0) and loads from the slot
+// the previous pass stored into; with PP (two buffers, bufs[0] and bufs[1]) consecutive
+// passes alternate slots and need no barrier between their loads and stores.
 template <int N, int Ns, int TwOff, int R, int... Rest> struct Run<N, Ns, TwOff, R, Rest...> {
-  template <int TB, int V, int NT, bool INV, bool FIRST, bool ZHI, int S, bool STEP, typename C, class L0, class SL>
-  static __device__ __forceinline__ void go(const C* tw, C* buf, const L0& first, const SL& last) {
+  template <int TB, int V, int NT, bool INV, bool FIRST, bool ZHI, int S, int STEP, bool PP, int K, typename C,
+            class L0, class SL>
+  static __device__ __forceinline__ void go(const C* tw, C* const* bufs, const L0& first, const SL& last) {
     constexpr bool LAST = sizeof...(Rest) == 0;
-    const Buf<C, TB, V, S, STEP> b{buf, N * TB};
+    constexpr int SO = PP ? K % 2 : 0, SI = PP ? (K + 1) % 2 : 0;
+    const Buf<C, TB, V, S, STEP, SO> bo{bufs[SO], N * TB};
+    const Buf<C, TB, V, S, STEP, SI> bi{bufs[SI], N * TB};
     if constexpr (FIRST && LAST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, last);
-    else if constexpr (FIRST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, b);
-    else if constexpr (LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, last);
-    else pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, b, b);
+    else if constexpr (FIRST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, bo);
+    else if constexpr (LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, bi, last);
+    else pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, bi, bo);
     if constexpr (!LAST)
-      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false, false, S, STEP>(
-          tw, buf, first, last);
+      Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false, false, S, STEP, PP,
+                                                                   K + 1>(tw, bufs, first, last);
   }
 };
 
@@ -301,10 +316,19 @@ template <int N, int... Rs> struct Plan {
   // first radix is even.
   static constexpr int first_r = FirstOf<Rs...>::r;        // radix of the first pass
   static constexpr bool can_zero_hi = first_r % 2 == 0;
-  template <int TB, int V, int NT, bool INV, bool ZHI = false, bool STEP = false, typename C, class L0, class SL>
+  template <int TB, int V, int NT, bool INV, bool ZHI = false, int STEP = 0, typename C, class L0, class SL>
   static __device__ __forceinline__ void run(const C* tw, C* buf, const L0& first, const SL& last) {
-    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r, STEP>(tw, buf, first,
-                                                                                              last);
+    C* const bufs[2] = {buf, buf};
+    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r, STEP, false, 0>(
+        tw, bufs, first, last);
+  }
+  // The same with two buffers: pass K stores into slot K mod 2 (a first loader that is a
+  // Buf of slot 1 reads bufs[1]).
+  template <int TB, int V, int NT, bool INV, bool ZHI = false, int STEP = 0, typename C, class L0, class SL>
+  static __device__ __forceinline__ void run2(const C* tw, C* buf0, C* buf1, const L0& first, const SL& last) {
+    C* const bufs[2] = {buf0, buf1};
+    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r, STEP, true, 0>(
+        tw, bufs, first, last);
   }
 };
 
