@@ -441,18 +441,72 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   }
 }
 
+// G^T y with the data spectrum in tensor memory (single precision, 256-thread CTAs): each
+// thread keeps the inputs of its first inverse-pass task (8 slots of two complex values,
+// 32 TMEM columns per half of the CTA's warps), which frees the second shared buffer for
+// passes that alternate between two buffers (Plan::run2).
+#ifndef TF_ADJ_TMPP
+#define TF_ADJ_TMPP 1
+#endif
+template <typename T, class P, int TB, int V, int NT> struct AdjTmem {
+  static constexpr int R0 = P::first_r, NB0 = P::n / R0, TOTAL0 = NB0 * (TB / V);
+  static constexpr bool on = TF_ADJ_TMPP && TF_COLS_TMEM && std::is_same<T, float>::value && NT == 256 &&
+                             V == 2 && TOTAL0 % 32 == 0 && TOTAL0 <= NT && R0 == 8;
+  static constexpr int kCols = 64;
+};
+
+// First inverse pass of G^T y's layer with the data spectrum in TMEM: a task's 8 inputs
+// (32 columns) in two 16-column loads, times conj(G_r) loaded from global memory first.
+template <typename C, int V> struct AdjSpecTask {
+  static constexpr bool kTaskLoad = true;
+  uint32_t tspec;
+  const C* spec;
+  int goff, hs, k0, nh, g_ext;
+  template <int R, int NB> __device__ __forceinline__ void task(int j, int b0, C (&v)[V][R]) const {
+    static_assert(V == 2 && R == 8, "32 TMEM columns per task");
+    const int k1 = k0 + b0;
+    C gv[R][V];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = goff + (j + r * NB) * hs + k1;
+      ld_row_vec<V, false>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteAdjSpec, e + V - 1, g_ext), gv[r]);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float f[16];
+      tmem::ld16(tspec + 16 * h, f);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v[0][4 * h + i] = cmulc(mk<C>(f[4 * i], f[4 * i + 1]), gv[4 * h + i][0]);
+        v[1][4 * h + i] = cmulc(mk<C>(f[4 * i + 2], f[4 * i + 3]), gv[4 * h + i][1]);
+      }
+    }
+  }
+};
+
 // Column stage of G^T y: forward transform of the data columns into shared memory, then
 // per layer the product with conj(G_r) and the inverse transform.
 template <typename T, class P, int TB, int V, int NT>
 __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? kWideThreadsPerSM : kAdjThreadsPerSM<T, P::n>)) k_cols_adj(const ColsAdj<T> a) {
   typedef typename CT<T>::C C;
+  typedef AdjTmem<T, P, TB, V, NT> AT;
   constexpr int N = P::n;
+  constexpr bool kTm = AT::on;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t tm_base;
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
   C* acc = buf + N * TB;
+  if constexpr (kTm)
+    if (threadIdx.x < 32) tmem::alloc(&tm_base, AT::kCols);
   for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  if constexpr (kTm) tmem::fence_before_sync();
   __syncthreads();
+  uint32_t tspec = 0;
+  if constexpr (kTm) {
+    tmem::fence_after_sync();
+    tspec = tmem::lane_addr(tm_base, (threadIdx.x >> 7) * (AT::kCols / 2));
+  }
   const int k0 = blockIdx.x * TB;
   const int nh = a.nh, hs = a.hs, ny = a.ny, sy = a.sy;
   const C* z = a.z + (int64_t)blockIdx.y * a.z_ld;
@@ -462,10 +516,31 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
     ld_row_vec<V, true>(z + j * hs + k1, k1, nh,
                   j >= 0 && j < sy && k1 < nh && TF_IN(kSiteAdjZ, j * hs + k1 + V - 1, z_ext), o);
   };
+  // the data spectrum in natural order: into acc, or with TMEM into the buffer that the
+  // two-buffer transform's last pass does not read (pass K reads slot (K + 1) mod 2)
+  C* const dsp = kTm && (P::npasses - 1) % 2 == 0 ? buf : acc;
   auto sacc = [=](int idx, int b0, const C* v, int) {
-    if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::st(acc + idx * TB + b0, v);
+    if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::st(dsp + idx * TB + b0, v);
   };
-  P::template run<TB, V, NT, false, false, kAdjStep>(tw, buf, load, sacc);
+  if constexpr (kTm) {
+    P::template run2<TB, V, NT, false, false, kAdjStep>(tw, buf, acc, load, sacc);
+    // slot r of a thread: input r of its first-pass task (element j + r NB0 of pair b0)
+    if (threadIdx.x < AT::TOTAL0) {
+      const int j = threadIdx.x / (TB / V), b0 = (threadIdx.x % (TB / V)) * V;
+#pragma unroll
+      for (int r = 0; r < AT::R0; ++r) {
+        C v[2] = {zero<C>(), zero<C>()};
+        const int e = (j + r * AT::NB0) * TB + b0;
+        if (TF_IN(kSiteSmem + 2, e + V - 1, N * TB)) Vec<V, C>::ld(dsp + e, v);
+        const float f[4] = {v[0].x, v[0].y, v[1].x, v[1].y};
+        tmem::st4(tspec + r * 4, f);
+      }
+    }
+    tmem::wait_st();
+    __syncthreads();
+  } else {
+    P::template run<TB, V, NT, false, false, kAdjStep>(tw, buf, load, sacc);
+  }
   C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
   const C* spec = a.spec;
   for (int r = 0; r < a.nz; ++r) {
@@ -485,7 +560,20 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
       const int e = uoff + idx * hs + k1;
       if (TF_IN(kSiteAdjU, e + V - 1, u_ext)) Vec<V, C>::st(u + e, v);
     };
-    P::template run<TB, V, NT, true, false, kAdjStep>(tw, buf, prod, store);
+    if constexpr (kTm) {
+      const AdjSpecTask<C, V> pt{tspec, spec, goff, hs, k0, nh, g_ext};
+      P::template run2<TB, V, NT, true, false, kAdjStep>(tw, buf, acc, pt, store);
+    } else {
+      P::template run<TB, V, NT, true, false, kAdjStep>(tw, buf, prod, store);
+    }
+  }
+  if constexpr (kTm) {
+    tmem::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      tmem::fence_after_sync();
+      tmem::dealloc(tm_base, AT::kCols);
+    }
   }
 }
 
@@ -575,7 +663,8 @@ template <typename T, class P>
 cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
   typedef ColTiles<T, P> TL;
   constexpr auto k = k_cols_adj<T, P, TL::TB, TL::V, TL::NT>;
-  const size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
+  size_t sm = (size_t)(twpad(P::n - 1) + 2 * P::n * TL::TB) * sizeof(typename CT<T>::C);
+  if (AdjTmem<T, P, TL::TB, TL::V, TL::NT>::on && sm < kTmemSmemFloor) sm = kTmemSmemFloor;
   cudaError_t e = set_smem<k>(sm);
   if (e != cudaSuccess) return e;
   k<<<dim3(cdiv(a.nh, TL::TB), ncols), TL::NT, sm, s>>>(a);

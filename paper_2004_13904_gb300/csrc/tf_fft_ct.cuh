@@ -132,6 +132,10 @@ template <typename C, int TB, int V, int S = 8, int STEP = 0, int SLOT = 0> stru
 
 template <class T, class = void> struct IsBuf : std::false_type {};
 template <class T> struct IsBuf<T, std::void_t<decltype(T::kIsBuf)>> : std::true_type {};
+// A loader that marks itself with kTaskLoad supplies a first pass's R inputs of one task
+// at once: task<R, NB>(j, b0, v) fills v[q][r] with element j + r NB of sequence b0 + q.
+template <class T, class = void> struct IsTaskLoad : std::false_type {};
+template <class T> struct IsTaskLoad<T, std::void_t<decltype(T::kTaskLoad)>> : std::true_type {};
 template <class L, class S, bool = IsBuf<L>::value && IsBuf<S>::value> struct SameBuf : std::false_type {};
 template <class L, class S> struct SameBuf<L, S, true> : std::bool_constant<L::kSlot == S::kSlot> {};
 
@@ -211,6 +215,10 @@ __device__ __forceinline__ void pass(const C* __restrict__ tw, const L& ld, cons
         e0 = at<C, TB, L::kS>(j, b0);
         if constexpr (LMODE == 2) e1 = at<C, TB, L::kS>(j + NB, b0);
       }
+      if constexpr (IsTaskLoad<L>::value) {
+        static_assert(Ns == 1 && !ZHI, "task loaders feed first passes");
+        ld.template task<R, NB>(j, b0, v[it]);
+      } else
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         C t[V];
@@ -310,6 +318,7 @@ template <int R, int... Rest> struct FirstOf { static constexpr int r = R; };
 
 template <int N, int... Rs> struct Plan {
   static constexpr int n = N;
+  static constexpr int npasses = (int)sizeof...(Rs);
   static constexpr int last_r = LastOf<Rs...>::r;          // radix of the last pass
   static constexpr int last_ns = LastOf<Rs...>::prod_before;  // its stride
   // The upper half of the input may be declared zero (run<..., ZHI = true>) when the

@@ -154,5 +154,13 @@ def test_forward_accumulator_tmem_budget():
         smem = max((tw + 2 * N * TB) * 8, floor)     # two buffers (ping-pong passes)
         resident = min(233472 // (smem + 1024), 2048 // NT)
         assert resident * alloc <= 512, (N, resident)
+        # cols_adj: the data spectrum in the 8 input slots of each thread's first
+        # inverse-pass task (at most one per thread, tasks filling whole warps), 64
+        # columns per CTA; every column CTA asks for at least the floor, so at most 4
+        # (forward or adjoint) share an SM: 4 x 128 columns at most
+        R0 = radices[0]
+        total0 = (N // R0) * (TB // V)
+        assert total0 % 32 == 0 and total0 <= NT and R0 == 8, (N, radices)
+        assert min(233472 // (max((tw + 2 * N * TB) * 8, floor) + 1024), 2048 // NT) * 128 <= 512
         used += 1
     assert used >= 3          # 320, 448 and 512
