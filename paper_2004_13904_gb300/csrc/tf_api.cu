@@ -627,8 +627,11 @@ tf_status tf_destroy(tf_op* op) {
   // A fault of earlier work surfaces here; report it rather than let the next call on
   // this device be the first to see it.
   const cudaError_t e = cudaDeviceSynchronize();
+  const unsigned pipe = e == cudaSuccess ? tfk::ct_pipe_status(true) : 0u;
   free_op(op);
-  return e == cudaSuccess ? TF_OK : cuda_fail(e, "work pending at tf_destroy");
+  if (e != cudaSuccess) return cuda_fail(e, "work pending at tf_destroy");
+  if (pipe) return fail(TF_ETIMEOUT, "a row kernel's bounded wait for its input copy ran out");
+  return TF_OK;
 }
 
 tf_status tf_dims(const tf_op* op, int64_t* m, int64_t* n) {

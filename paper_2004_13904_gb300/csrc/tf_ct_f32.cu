@@ -13,6 +13,16 @@ const MenuEntry kMenu[] = {TF_CT_MENU(TF_CT_MENU_ENTRY)};
 #undef TF_CT_MENU_ENTRY
 }  // namespace
 
+unsigned ct_pipe_status(bool clear) {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, ctk::g_pipe_status, sizeof(v)) != cudaSuccess) return 0;
+  if (clear && v) {
+    const unsigned z = 0;
+    cudaMemcpyToSymbol(ctk::g_pipe_status, &z, sizeof(z));
+  }
+  return v;
+}
+
 int ct_menu_count() { return (int)(sizeof(kMenu) / sizeof(kMenu[0])); }
 int ct_menu_length(int i) { return kMenu[i].n; }
 int ct_menu_radices(int i, int* radices) {

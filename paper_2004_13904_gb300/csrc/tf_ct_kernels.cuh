@@ -6,6 +6,7 @@
 #include <atomic>
 #include <type_traits>
 
+#include "tf_bulk.cuh"
 #include "tf_check.cuh"
 #include "tf_fft_ct.cuh"
 #include "tf_internal.h"
@@ -237,6 +238,219 @@ __global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT, 1280)) k_rows_c2r(c
         dst[o] = (scale && TF_IN(kSiteC2rScale, o, dst_ext)) ? y[j] * scale[o] : y[j];
     }
   });
+}
+
+// Persistent row kernels with bulk copies (single precision).  A tile is the 2 TB real rows
+// that the plain row kernels give one CTA; its rows are consecutive in memory, so the
+// input is one contiguous block and so is the output.  Each CTA walks the tiles of all
+// columns (stride gridDim.x).  One thread moves a tile's input into shared memory with one
+// bulk copy, issued as soon as the previous tile is staged, so it lands while the CTA
+// transforms; the unpacked output goes to a shared-memory tile in the global layout and
+// leaves with one bulk store that completes while the CTA works on the next tile.  DRAM
+// latency is hidden by the copies in flight instead of by resident warps, so the kernels
+// run two CTAs per SM with the register budget that needs.
+// The output tile of rows_r2c includes each row's padding [nh, hs), zeroed once, so the
+// workspace's padding stays zero.  Every wait on the input barrier is bounded: past
+// kPipeWaitNs the CTA records TF_ETIMEOUT in the status word and returns.
+constexpr unsigned long long kPipeWaitNs = 2000000000ull;
+constexpr int kPipeStatusTimeout = 6;   // TF_ETIMEOUT
+struct RowsPipe {
+  int tiles_per_col, ncols;
+  unsigned int* status;
+};
+#ifndef TF_ROWS_PIPE_STEP
+#define TF_ROWS_PIPE_STEP 0
+#endif
+
+template <typename T, class P, int TB, int V, int NT, bool ZHI>
+__global__ void __launch_bounds__(NT, 2) k_rows_r2c_pipe(const RowsR2C<T> a, const RowsPipe pp) {
+  typedef typename CT<T>::C C;
+  constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2, RT = 2 * TB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  const int len = a.row_len, hs = a.hs, nrows = a.nrows, off = a.seq_off, tpc = pp.tiles_per_col;
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + twpad(N - 1);
+  C* out = buf + N * TB;                          // [RT][hs], the global layout
+  T* in = reinterpret_cast<T*>(out + RT * hs);    // [RT][len]
+  const int64_t ntiles = (int64_t)tpc * pp.ncols;
+  auto issue = [&](int64_t t) {
+    const int col = (int)(t / tpc), tile = (int)(t - (int64_t)col * tpc);
+    const int rows = min(RT, nrows - tile * RT);
+    const uint32_t bytes = (uint32_t)(rows * len * sizeof(T));
+    bulk::mbar_expect_tx(&bar, bytes);
+    bulk::load(in, a.src + (int64_t)col * a.src_ld + (int64_t)tile * RT * len, bytes, &bar);
+  };
+  if (threadIdx.x == 0) {
+    bulk::mbar_init(&bar, 1);
+    bulk::fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  for (int i = threadIdx.x; i < RT * (hs - NH); i += NT) out[(i / (hs - NH)) * hs + NH + i % (hs - NH)] = zero<C>();
+  __syncthreads();
+  if (threadIdx.x == 0 && (int64_t)blockIdx.x < ntiles) issue(blockIdx.x);
+  constexpr int NS = ZHI && P::can_zero_hi ? N / 2 : N;
+  uint32_t phase = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const bool ok = bulk::mbar_wait_bounded(&bar, phase, kPipeWaitNs);
+    phase ^= 1;
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(pp.status, (unsigned)kPipeStatusTimeout);
+        bulk::wait_all();
+      }
+      return;
+    }
+    const int col = (int)(t / tpc), tile = (int)(t - (int64_t)col * tpc);
+    const int rows = min(RT, nrows - tile * RT);
+    const T* scale = a.scale ? a.scale + (int64_t)tile * RT * len : nullptr;
+    visit_pairs<NT, TP>(NS, [&](int n, int q) {
+      const ct::RowAt<C, TB, P::first_r> ra(n);
+      const int e = n - off;
+      T x[4] = {T(0), T(0), T(0), T(0)};
+      if (e >= 0 && e < len) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = 4 * q + i;
+          if (r >= rows) break;
+          x[i] = in[r * len + e];
+          if (scale) x[i] *= scale[r * len + e];
+        }
+      }
+      const C v[2] = {mk<C>(x[0], x[1]), mk<C>(x[2], x[3])};
+      const int p = ra(2 * q);
+      if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::st(buf + p, v);
+    });
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (t + gridDim.x < ntiles) {
+        bulk::fence_proxy_async();
+        issue(t + gridDim.x);
+      }
+      bulk::wait_read_all();   // the previous tile's output has left `out`
+    }
+    const ct::Buf<C, TB, V, P::first_r, TF_ROWS_PIPE_STEP> b{buf, N * TB};
+    P::template run<TB, V, NT, false, ZHI, TF_ROWS_PIPE_STEP>(tw, buf, b, b);
+    visit_pairs<NT, TP>(NH, [&](int k, int q) {
+      const int r0 = 4 * q;
+      if (r0 >= rows) return;
+      const ct::RowAt<C, TB, P::first_r> rk(k), rc(k ? N - k : 0);
+      C z[2], zc[2];
+      const int pk = rk(2 * q), pc = rc(2 * q);
+      if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::ld(buf + pk, z);
+      if (TF_IN(kSiteSmem + 3, pc + 1, N * TB)) Vec<2, C>::ld(buf + pc, zc);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ra = r0 + 2 * h, rb = ra + 1;
+        if (ra >= rows) break;
+        zc[h].y = -zc[h].y;
+        out[ra * hs + k] = mk<C>(T(0.5) * (z[h].x + zc[h].x), T(0.5) * (z[h].y + zc[h].y));
+        if (rb < rows) out[rb * hs + k] = mk<C>(T(0.5) * (z[h].y - zc[h].y), T(-0.5) * (z[h].x - zc[h].x));
+      }
+    });
+    bulk::fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bulk::store(a.dst + (int64_t)col * a.dst_ld + (int64_t)tile * RT * hs, out, (uint32_t)(rows * hs * sizeof(C)));
+      bulk::commit();
+    }
+  }
+  if (threadIdx.x == 0) bulk::wait_all();
+}
+
+template <typename T, class P, int TB, int V, int NT>
+__global__ void __launch_bounds__(NT, 2) k_rows_c2r_pipe(const RowsC2R<T> a, const RowsPipe pp) {
+  typedef typename CT<T>::C C;
+  constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2, RT = 2 * TB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  const int hs = a.hs, nrows = a.nrows, L = a.out_len, off = a.seq_off, tpc = pp.tiles_per_col;
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + twpad(N - 1);
+  C* in = buf + N * TB;                           // [RT][hs]
+  T* out = reinterpret_cast<T*>(in + RT * hs);    // [RT][L], the global layout
+  const int64_t ntiles = (int64_t)tpc * pp.ncols;
+  auto issue = [&](int64_t t) {
+    const int col = (int)(t / tpc), tile = (int)(t - (int64_t)col * tpc);
+    const int rows = min(RT, nrows - tile * RT);
+    const uint32_t bytes = (uint32_t)(rows * hs * sizeof(C));
+    bulk::mbar_expect_tx(&bar, bytes);
+    bulk::load(in, a.src + (int64_t)col * a.src_ld + (int64_t)tile * RT * hs, bytes, &bar);
+  };
+  if (threadIdx.x == 0) {
+    bulk::mbar_init(&bar, 1);
+    bulk::fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
+  __syncthreads();
+  if (threadIdx.x == 0 && (int64_t)blockIdx.x < ntiles) issue(blockIdx.x);
+  uint32_t phase = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const bool ok = bulk::mbar_wait_bounded(&bar, phase, kPipeWaitNs);
+    phase ^= 1;
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(pp.status, (unsigned)kPipeStatusTimeout);
+        bulk::wait_all();
+      }
+      return;
+    }
+    const int col = (int)(t / tpc), tile = (int)(t - (int64_t)col * tpc);
+    const int rows = min(RT, nrows - tile * RT);
+    visit_pairs<NT, TP>(NH, [&](int k, int q) {
+      const bool self = (k == 0) || (2 * k == N);
+      const int r0 = 4 * q;
+      C x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = r0 + i < rows ? in[(r0 + i) * hs + k] : zero<C>();
+      C lo[2], hi[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        C xa = x[2 * h], xb = x[2 * h + 1];
+        if (self) { xa.y = T(0); xb.y = T(0); }
+        lo[h] = mk<C>(xa.x - xb.y, xa.y + xb.x);
+        hi[h] = mk<C>(xa.x + xb.y, xb.x - xa.y);
+      }
+      const int pk = ct::RowAt<C, TB, P::first_r>(k)(2 * q);
+      if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::st(buf + pk, lo);
+      if (!self) {
+        const int pc = ct::RowAt<C, TB, P::first_r>(N - k)(2 * q);
+        if (TF_IN(kSiteSmem + 3, pc + 1, N * TB)) Vec<2, C>::st(buf + pc, hi);
+      }
+    });
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (t + gridDim.x < ntiles) {
+        bulk::fence_proxy_async();
+        issue(t + gridDim.x);
+      }
+      bulk::wait_read_all();
+    }
+    const ct::Buf<C, TB, V, P::first_r, TF_ROWS_PIPE_STEP> b{buf, N * TB};
+    P::template run<TB, V, NT, true, false, TF_ROWS_PIPE_STEP>(tw, buf, b, b);
+    const T* scale = a.scale ? a.scale + (int64_t)tile * RT * L : nullptr;
+    visit_pairs<NT, TP>(L, [&](int i, int q) {
+      const int r0 = 4 * q;
+      if (r0 >= rows) return;
+      C z[2];
+      const int p = ct::RowAt<C, TB, P::first_r>(off + i)(2 * q);
+      if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::ld(buf + p, z);
+      const T y[4] = {z[0].x, z[0].y, z[1].x, z[1].y};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (r0 + j >= rows) break;
+        const int o = (r0 + j) * L + i;
+        out[o] = scale ? y[j] * scale[o] : y[j];
+      }
+    });
+    bulk::fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bulk::store(a.dst + (int64_t)col * a.dst_ld + (int64_t)tile * RT * L, out, (uint32_t)(rows * L * sizeof(T)));
+      bulk::commit();
+    }
+  }
+  if (threadIdx.x == 0) bulk::wait_all();
 }
 
 // Spectrum values are staged in registers ahead of use in single precision only (the
@@ -627,9 +841,109 @@ template <typename T, class P> struct ColTiles<T, P, true> {
   static constexpr int TB = 8, V = 2, NT = 64;
 };
 
+// The persistent bulk-copy row kernels serve single-precision plans on 256-thread CTAs
+// (n > 256) when every tile's input and output block starts on a 16-byte boundary and
+// spans a multiple of 16 bytes; other launches take the per-tile kernels above.
+#ifndef TF_ROWS_PIPE
+#define TF_ROWS_PIPE 1
+#endif
+static __device__ unsigned int g_pipe_status;   // TF_ETIMEOUT after a wait ran out
+template <typename T, class P> constexpr bool kRowsPipe =
+    TF_ROWS_PIPE && std::is_same<T, float>::value && Tiles<T, P::n>::NT == 256;
+
+inline bool aligned16(const void* p, int64_t ld_bytes) {
+  return ((uintptr_t)p & 15) == 0 && ld_bytes % 16 == 0;
+}
+// A block of `rows` rows of `row_bytes` each, for full tiles and the tail tile.
+inline bool tiles_ok(int nrows, int rt, int64_t row_bytes) {
+  const int tail = nrows % rt;
+  return (rt * row_bytes) % 16 == 0 && (tail * row_bytes) % 16 == 0;
+}
+struct PipeDev {
+  int sms = 0;
+  unsigned int* status = nullptr;
+};
+inline cudaError_t pipe_dev(PipeDev* out) {
+  static PipeDev per[kSmemDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kSmemDevices) return cudaErrorNotSupported;
+  if (!per[dev].status) {
+    PipeDev d;
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaGetSymbolAddress((void**)&d.status, g_pipe_status);
+    if (e != cudaSuccess) return e;
+    per[dev] = d;
+  }
+  *out = per[dev];
+  return cudaSuccess;
+}
+
+template <typename T, class P>
+cudaError_t rows_r2c_pipe(const RowsR2C<T>& a, int ncols, cudaStream_t s, bool* used) {
+  typedef Tiles<T, P::n> TL;
+  constexpr int RT = 2 * TL::TB;
+  typedef typename CT<T>::C C;
+  *used = false;
+  if (!aligned16(a.src, a.src_ld * (int64_t)sizeof(T)) || !aligned16(a.dst, a.dst_ld * (int64_t)sizeof(C)) ||
+      !tiles_ok(a.nrows, RT, (int64_t)a.row_len * sizeof(T)))
+    return cudaSuccess;
+  PipeDev d;
+  if (pipe_dev(&d) != cudaSuccess) return cudaSuccess;
+  const size_t in_bytes = ((size_t)RT * a.row_len * sizeof(T) + 15) & ~(size_t)15;
+  const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB + RT * a.hs) * sizeof(C) + in_bytes;
+  RowsPipe pp{(a.nrows + RT - 1) / RT, ncols, d.status};
+  const int64_t ntiles = (int64_t)pp.tiles_per_col * ncols;
+  const int grid = (int)std::min<int64_t>(ntiles, 2 * (int64_t)d.sms);
+  if (grid <= 0) return cudaSuccess;
+  *used = true;
+  const bool zhi = P::can_zero_hi && a.seq_off >= 0 && a.seq_off + a.row_len <= P::n / 2;
+  cudaError_t e;
+  if (zhi) {
+    constexpr auto k = k_rows_r2c_pipe<T, P, TL::TB, TL::V, TL::NT, true>;
+    e = set_smem<k>(sm);
+    if (e == cudaSuccess) k<<<grid, TL::NT, sm, s>>>(a, pp);
+  } else {
+    constexpr auto k = k_rows_r2c_pipe<T, P, TL::TB, TL::V, TL::NT, false>;
+    e = set_smem<k>(sm);
+    if (e == cudaSuccess) k<<<grid, TL::NT, sm, s>>>(a, pp);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+template <typename T, class P>
+cudaError_t rows_c2r_pipe(const RowsC2R<T>& a, int ncols, cudaStream_t s, bool* used) {
+  typedef Tiles<T, P::n> TL;
+  constexpr int RT = 2 * TL::TB;
+  typedef typename CT<T>::C C;
+  *used = false;
+  if (!aligned16(a.src, a.src_ld * (int64_t)sizeof(C)) || !aligned16(a.dst, a.dst_ld * (int64_t)sizeof(T)) ||
+      !tiles_ok(a.nrows, RT, (int64_t)a.out_len * sizeof(T)))
+    return cudaSuccess;
+  PipeDev d;
+  if (pipe_dev(&d) != cudaSuccess) return cudaSuccess;
+  const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB + RT * a.hs) * sizeof(C) +
+                    (((size_t)RT * a.out_len * sizeof(T) + 15) & ~(size_t)15);
+  RowsPipe pp{(a.nrows + RT - 1) / RT, ncols, d.status};
+  const int64_t ntiles = (int64_t)pp.tiles_per_col * ncols;
+  const int grid = (int)std::min<int64_t>(ntiles, 2 * (int64_t)d.sms);
+  if (grid <= 0) return cudaSuccess;
+  *used = true;
+  constexpr auto k = k_rows_c2r_pipe<T, P, TL::TB, TL::V, TL::NT>;
+  cudaError_t e = set_smem<k>(sm);
+  if (e == cudaSuccess) k<<<grid, TL::NT, sm, s>>>(a, pp);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <typename T, class P>
 cudaError_t rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
+  if constexpr (kRowsPipe<T, P>) {
+    bool used = false;
+    const cudaError_t e = rows_r2c_pipe<T, P>(a, ncols, s, &used);
+    if (used || e != cudaSuccess) return e;
+  }
   const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB) * sizeof(typename CT<T>::C);
   const dim3 grid(cdiv((a.nrows + 1) / 2, TL::TB), ncols);
   if (P::can_zero_hi && a.seq_off >= 0 && a.seq_off + a.row_len <= P::n / 2)
@@ -639,6 +953,11 @@ cudaError_t rows_r2c(const RowsR2C<T>& a, int ncols, cudaStream_t s) {
 template <typename T, class P>
 cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
   typedef Tiles<T, P::n> TL;
+  if constexpr (kRowsPipe<T, P>) {
+    bool used = false;
+    const cudaError_t e = rows_c2r_pipe<T, P>(a, ncols, s, &used);
+    if (used || e != cudaSuccess) return e;
+  }
   constexpr auto k = k_rows_c2r<T, P, TL::TB, TL::V, TL::NT>;
   const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB) * sizeof(typename CT<T>::C);
   cudaError_t e = set_smem<k>(sm);

@@ -150,6 +150,9 @@ template <> cudaError_t ct_cols_fwd<float>(const ColsFwd<float>&, int, cudaStrea
 template <> cudaError_t ct_cols_fwd<double>(const ColsFwd<double>&, int, cudaStream_t);
 template <> cudaError_t ct_cols_adj<float>(const ColsAdj<float>&, int, cudaStream_t);
 template <> cudaError_t ct_cols_adj<double>(const ColsAdj<double>&, int, cudaStream_t);
+// Status word of the persistent bulk-copy row kernels: TF_ETIMEOUT (6) once a bounded wait
+// ran out, else 0; `clear` resets it.
+unsigned ct_pipe_status(bool clear);
 // Transform lengths that have compile-time plans (ascending), with their radix lists.
 int ct_menu_count();
 int ct_menu_length(int i);
