@@ -58,6 +58,15 @@ __device__ __forceinline__ void load(void* dst, const void* src, uint32_t bytes,
                "l"(src), "r"(bytes), "r"(saddr(bar))
                : "memory");
 }
+// 2-D tile of a tensor map (a __grid_constant__ kernel parameter) at element coordinates
+// (x, y) -> shared memory (128-byte aligned), completion counted on `bar`
+__device__ __forceinline__ void load_tile_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
 // shared -> global, in the thread's current bulk group
 __device__ __forceinline__ void store(void* dst, const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(saddr(src)),

@@ -3,6 +3,8 @@
 // tf_kernels.cu compute (same stages, same data layout, same twiddle tables); only the
 // index arithmetic is resolved at compile time.  Included by tf_ct_f32.cu / tf_ct_f64.cu.
 #pragma once
+#include <cuda.h>
+
 #include <atomic>
 #include <type_traits>
 
@@ -253,6 +255,7 @@ __global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT, 1280)) k_rows_c2r(c
 // workspace's padding stays zero.  Every wait on the input barrier is bounded: past
 // kPipeWaitNs the CTA records TF_ETIMEOUT in the status word and returns.
 constexpr unsigned long long kPipeWaitNs = 2000000000ull;
+static __device__ unsigned int g_pipe_status;   // TF_ETIMEOUT after a wait ran out
 constexpr int kPipeStatusTimeout = 6;   // TF_ETIMEOUT
 struct RowsPipe {
   int tiles_per_col, ncols;
@@ -495,8 +498,8 @@ constexpr size_t kTmemSmemFloor = 47104;   // > 228 KB / 5 - 1 KB: at most 4 res
 // precision each thread loads the spectrum values that its last forward pass multiplies
 // at the start of every layer, into registers, so that their global-memory latency
 // overlaps the layer's first passes.
-template <typename T, class P, int TB, int V, int NT, bool ZHI>
-__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? kWideThreadsPerSM : kFwdThreadsPerSM<T>)) k_cols_fwd(const ColsFwd<T> a) {
+template <typename T, class P, int TB, int V, int NT, bool ZHI, bool TILE>
+__global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? kWideThreadsPerSM : kFwdThreadsPerSM<T>)) k_cols_fwd(const ColsFwd<T> a, const __grid_constant__ CUtensorMap zmap) {
   typedef typename CT<T>::C C;
   typedef FwdTmem<T, P, TB, V, NT> FT;
   constexpr int N = P::n;
@@ -513,13 +516,26 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   // consecutive passes alternate between them (Plan::run2: no barrier inside a pass)
   constexpr bool kPP = FT::pp;
   static_assert(!kPP || FT::nbuf == 2, "ping-pong needs the second buffer");
+  // TILE: each layer's row-transformed tile of a model column ([ny][TB]) arrives in shared
+  // memory by one tensor copy (zmap: the workspace as rows of 2 hs floats, box TB x ny),
+  // issued right after the column's previous layer, and the first pass reads it there
+  constexpr bool kTile = TILE && kTm;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t tm_base;
+  __shared__ __align__(8) uint64_t zbar[MC];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
   C* acc = buf + N * TB;
+  // [MC][ny][TB] with TILE, 128-byte aligned (the launch adds 128 bytes)
+  C* ztile = reinterpret_cast<C*>((reinterpret_cast<uintptr_t>(acc + N * TB) + 127) & ~(uintptr_t)127);
   if constexpr (kTm)
     if (threadIdx.x < 32) tmem::alloc(&tm_base, FT::kCols);
+  if constexpr (kTile)
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int c = 0; c < MC; ++c) bulk::mbar_init(&zbar[c], 1);
+      bulk::fence_mbar_init();
+    }
   for (int i = threadIdx.x; i < N - 1; i += NT) tw[i] = a.tw[i];
   if constexpr (kTm) tmem::fence_before_sync();
   __syncthreads();
@@ -541,6 +557,16 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   const int mc = MC > 1 && a.ncols - col0 < MC ? a.ncols - col0 : MC;   // the CTA's columns
   const int z_ext = a.nz * ny * hs, g_ext = a.nz * N * hs, s_ext = sy * hs;
   const C* spec = a.spec;
+  const int zrows = (int)(a.z_ld / hs);   // workspace rows per model column
+  auto issue = [&](int c, int r) {
+    if (threadIdx.x == 0) {
+      bulk::fence_proxy_async();
+      bulk::mbar_expect_tx(&zbar[c], (uint32_t)(ny * TB * sizeof(C)));
+      bulk::load_tile_2d(ztile + c * ny * TB, &zmap, 2 * k0, (col0 + c) * zrows + r * ny, &zbar[c]);
+    }
+  };
+  if constexpr (kTile)
+    for (int c = 0; c < mc; ++c) issue(c, 0);
   C gpre[kPre ? ITL * RL : 1][V];
   for (int r = 0; r < a.nz; ++r) {
     const int zoff = r * ny * hs, goff = r * N * hs;
@@ -566,10 +592,33 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
       // zeroed when allocated, the row kernels never write its padding, and the column
       // kernels write zeros there (their padded sequences have zero inputs).  A masked load
       // measured much slower here (the mask's select waits for the load).
+      if constexpr (kTile) {
+        const bool ok = bulk::mbar_wait_bounded(&zbar[c], r & 1, kPipeWaitNs);
+        if (__syncthreads_or(!ok)) {   // a copy never completed: report, free TMEM, return
+          tmem::fence_before_sync();
+          __syncthreads();
+          if (threadIdx.x < 32) {
+            tmem::fence_after_sync();
+            tmem::dealloc(tm_base, FT::kCols);
+          }
+          if (threadIdx.x == 0) atomicExch(&g_pipe_status, (unsigned)kPipeStatusTimeout);
+          return;
+        }
+      }
+      const C* zt = ztile + c * ny * TB;
       auto load = [=](int idx, int b0, C* o) {
-        const int k1 = k0 + b0;
-        const int e = zoff + idx * hs + k1;
-        ld_row_vec<V, false>(z + e, k1, nh, idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e + V - 1, z_ext), o);
+        if constexpr (kTile) {
+          if (idx < ny && TF_IN(kSiteSmem + 4, idx * TB + b0 + V - 1, ny * TB)) {
+            Vec<V, C>::ld(zt + idx * TB + b0, o);
+          } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q) o[q] = zero<C>();
+          }
+        } else {
+          const int k1 = k0 + b0;
+          const int e = zoff + idx * hs + k1;
+          ld_row_vec<V, false>(z + e, k1, nh, idx < ny && k1 < nh && TF_IN(kSiteFwdZ, e + V - 1, z_ext), o);
+        }
       };
       auto mac = [&](int idx, int b0, const C* v, int slot) {
         if constexpr (kTm) {
@@ -607,6 +656,8 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
       if constexpr (kPP) P::template run2<TB, V, NT, false, ZHI, 3>(tw, buf, acc, load, mac);
       else P::template run<TB, V, NT, false, ZHI, 3>(tw, buf, load, mac);
       if constexpr (kTm) tmem::wait_st();
+      if constexpr (kTile)
+        if (r + 1 < a.nz) issue(c, r + 1);   // the passes ended at a barrier: the tile is free
     }
   }
   for (int c = 0; c < MC; ++c) {
@@ -847,7 +898,6 @@ template <typename T, class P> struct ColTiles<T, P, true> {
 #ifndef TF_ROWS_PIPE
 #define TF_ROWS_PIPE 1
 #endif
-static __device__ unsigned int g_pipe_status;   // TF_ETIMEOUT after a wait ran out
 template <typename T, class P> constexpr bool kRowsPipe =
     TF_ROWS_PIPE && std::is_same<T, float>::value && Tiles<T, P::n>::NT == 256;
 
@@ -965,6 +1015,47 @@ cudaError_t rows_c2r(const RowsC2R<T>& a, int ncols, cudaStream_t s) {
   k<<<dim3(cdiv((a.nrows + 1) / 2, TL::TB), ncols), TL::NT, sm, s>>>(a);
   return cudaGetLastError();
 }
+#ifndef TF_FWD_TILE
+#define TF_FWD_TILE 1
+#endif
+template <auto K, class A>
+cudaError_t launch_fwd(const A& a, const CUtensorMap& m, dim3 grid, int nt, size_t sm, cudaStream_t s) {
+  cudaError_t e = set_smem<K>(sm);
+  if (e != cudaSuccess) return e;
+  K<<<grid, nt, sm, s>>>(a, m);
+  return cudaGetLastError();
+}
+// The column-stage workspace of `ncols` columns as a 2-D tensor of single-precision values:
+// rows of 2 hs floats (stride hs complex values), z_ld / hs rows per column; box 2 TB x ny.
+// False when the driver entry point is missing or the layout does not fit a tensor map.
+template <typename T>
+bool encode_rows_map(const ColsFwd<T>& a, int ncols, int tb, CUtensorMap* m) {
+  typedef CUresult (*Encode)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode enc = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<Encode>(fn);
+    looked = true;
+  }
+  if (!enc || !std::is_same<T, float>::value) return false;
+  if (((uintptr_t)a.z & 15) != 0 || a.z_ld % a.hs != 0 || (a.hs * 8) % 16 != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * a.hs, (cuuint64_t)(a.z_ld / a.hs) * (cuuint64_t)ncols};
+  const cuuint64_t strides[1] = {(cuuint64_t)a.hs * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * tb), (cuuint32_t)a.ny};
+  const cuuint32_t estr[2] = {1, 1};
+  if (dims[1] >= (1ull << 32)) return false;
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)a.z, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+constexpr size_t kFwdTileSmemMax = 228 * 1024 / 2 - 1024 - 256;   // two CTAs per SM
 template <typename T, class P>
 cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
   typedef ColTiles<T, P> TL;
@@ -975,8 +1066,20 @@ cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
   const dim3 grid(cdiv(a.nh, TL::TB), cdiv(ncols, FT::MC));
   ColsFwd<T> ac = a;
   ac.ncols = ncols;
-  if (zhi) return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, true>>(ac, grid, TL::NT, sm, s);
-  return launch_k<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, false>>(ac, grid, TL::NT, sm, s);
+  CUtensorMap zmap;
+  memset(&zmap, 0, sizeof(zmap));
+  if constexpr (FT::on && TF_FWD_TILE) {
+    // tensor-copied layer tiles: a box of TB values by ny rows, and room for the tiles
+    // within the two CTAs per SM that the register budget allows
+    typedef typename CT<T>::C C;
+    const size_t st = sm + 128 + (size_t)FT::MC * a.ny * TL::TB * sizeof(C);
+    if (a.ny <= 256 && st <= kFwdTileSmemMax && encode_rows_map(a, ncols, TL::TB, &zmap)) {
+      if (zhi) return launch_fwd<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, true, true>>(ac, zmap, grid, TL::NT, st, s);
+      return launch_fwd<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, false, true>>(ac, zmap, grid, TL::NT, st, s);
+    }
+  }
+  if (zhi) return launch_fwd<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, true, false>>(ac, zmap, grid, TL::NT, sm, s);
+  return launch_fwd<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, false, false>>(ac, zmap, grid, TL::NT, sm, s);
 }
 template <typename T, class P>
 cudaError_t cols_adj(const ColsAdj<T>& a, int ncols, cudaStream_t s) {
