@@ -292,7 +292,6 @@ __global__ void __launch_bounds__(NT, 2) k_rows_r2c_pipe(const RowsR2C<T> a, con
   for (int i = threadIdx.x; i < RT * (hs - NH); i += NT) out[(i / (hs - NH)) * hs + NH + i % (hs - NH)] = zero<C>();
   __syncthreads();
   if (threadIdx.x == 0 && (int64_t)blockIdx.x < ntiles) issue(blockIdx.x);
-  constexpr int NS = ZHI && P::can_zero_hi ? N / 2 : N;
   uint32_t phase = 0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const bool ok = bulk::mbar_wait_bounded(&bar, phase, kPipeWaitNs);
@@ -307,33 +306,38 @@ __global__ void __launch_bounds__(NT, 2) k_rows_r2c_pipe(const RowsR2C<T> a, con
     const int col = (int)(t / tpc), tile = (int)(t - (int64_t)col * tpc);
     const int rows = min(RT, nrows - tile * RT);
     const T* scale = a.scale ? a.scale + (int64_t)tile * RT * len : nullptr;
-    visit_pairs<NT, TP>(NS, [&](int n, int q) {
-      const ct::RowAt<C, TB, P::first_r> ra(n);
-      const int e = n - off;
-      T x[4] = {T(0), T(0), T(0), T(0)};
-      if (e >= 0 && e < len) {
+    // the first pass reads the rows where the copy left them: sequence b holds rows 2b
+    // (real part) and 2b + 1 (imaginary part)
+    auto ld_in = [=](int idx, int b0, C* o) {
+      const int e = idx - off;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int r = 4 * q + i;
-          if (r >= rows) break;
-          x[i] = in[r * len + e];
-          if (scale) x[i] *= scale[r * len + e];
+      for (int q = 0; q < V; ++q) {
+        const int ra = 2 * (b0 + q);
+        T x0 = T(0), x1 = T(0);
+        if (e >= 0 && e < len) {
+          if (ra < rows) x0 = in[ra * len + e];
+          if (ra + 1 < rows) x1 = in[(ra + 1) * len + e];
+          if (scale) {
+            x0 *= scale[ra * len + e];
+            x1 *= ra + 1 < rows ? scale[(ra + 1) * len + e] : T(0);
+          }
         }
+        o[q] = mk<C>(x0, x1);
       }
-      const C v[2] = {mk<C>(x[0], x[1]), mk<C>(x[2], x[3])};
-      const int p = ra(2 * q);
-      if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::st(buf + p, v);
-    });
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (t + gridDim.x < ntiles) {
-        bulk::fence_proxy_async();
-        issue(t + gridDim.x);
+    };
+    // after the first pass: the next tile's input may overwrite `in`, and the previous
+    // tile's output must have left `out` before the unpacking below
+    auto hook = [&]() {
+      if (threadIdx.x == 0) {
+        if (t + gridDim.x < ntiles) {
+          bulk::fence_proxy_async();
+          issue(t + gridDim.x);
+        }
+        bulk::wait_read_all();
       }
-      bulk::wait_read_all();   // the previous tile's output has left `out`
-    }
+    };
     const ct::Buf<C, TB, V, P::first_r, TF_ROWS_PIPE_STEP> b{buf, N * TB};
-    P::template run<TB, V, NT, false, ZHI, TF_ROWS_PIPE_STEP>(tw, buf, b, b);
+    P::template run_h<TB, V, NT, false, ZHI, TF_ROWS_PIPE_STEP>(tw, buf, ld_in, b, hook);
     visit_pairs<NT, TP>(NH, [&](int k, int q) {
       const int r0 = 4 * q;
       if (r0 >= rows) return;
@@ -361,24 +365,29 @@ __global__ void __launch_bounds__(NT, 2) k_rows_r2c_pipe(const RowsR2C<T> a, con
   if (threadIdx.x == 0) bulk::wait_all();
 }
 
+// Rows of the c2r input tile sit at row * hs + 4 (row / 4) values: the first pass's loads
+// of rows 0, 4, 8, 12 (one per sequence pair of a half-warp) then fall in different banks.
+__host__ __device__ constexpr int c2r_in_row(int r, int hs) { return r * hs + 4 * (r >> 2); }
+
 template <typename T, class P, int TB, int V, int NT>
 __global__ void __launch_bounds__(NT, 2) k_rows_c2r_pipe(const RowsC2R<T> a, const RowsPipe pp) {
   typedef typename CT<T>::C C;
-  constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2, RT = 2 * TB;
+  constexpr int N = P::n, RT = 2 * TB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   const int hs = a.hs, nrows = a.nrows, L = a.out_len, off = a.seq_off, tpc = pp.tiles_per_col;
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
-  C* in = buf + N * TB;                           // [RT][hs]
-  T* out = reinterpret_cast<T*>(in + RT * hs);    // [RT][L], the global layout
+  C* in = buf + N * TB;                                   // rows at c2r_in_row
+  T* out = reinterpret_cast<T*>(in + c2r_in_row(RT, hs));  // [RT][L], the global layout
   const int64_t ntiles = (int64_t)tpc * pp.ncols;
   auto issue = [&](int64_t t) {
     const int col = (int)(t / tpc), tile = (int)(t - (int64_t)col * tpc);
     const int rows = min(RT, nrows - tile * RT);
-    const uint32_t bytes = (uint32_t)(rows * hs * sizeof(C));
-    bulk::mbar_expect_tx(&bar, bytes);
-    bulk::load(in, a.src + (int64_t)col * a.src_ld + (int64_t)tile * RT * hs, bytes, &bar);
+    const C* src = a.src + (int64_t)col * a.src_ld + (int64_t)tile * RT * hs;
+    bulk::mbar_expect_tx(&bar, (uint32_t)(rows * hs * sizeof(C)));
+    for (int r = 0; r < rows; ++r)
+      bulk::load(in + c2r_in_row(r, hs), src + (int64_t)r * hs, (uint32_t)(hs * sizeof(C)), &bar);
   };
   if (threadIdx.x == 0) {
     bulk::mbar_init(&bar, 1);
@@ -400,52 +409,45 @@ __global__ void __launch_bounds__(NT, 2) k_rows_c2r_pipe(const RowsC2R<T> a, con
     }
     const int col = (int)(t / tpc), tile = (int)(t - (int64_t)col * tpc);
     const int rows = min(RT, nrows - tile * RT);
-    visit_pairs<NT, TP>(NH, [&](int k, int q) {
+    // first pass: element idx of sequence b = Xa[idx] + i Xb[idx], the Hermitian extensions
+    // of the half spectra of rows 2b and 2b + 1 (X[N - k] = conj X[k]; the imaginary parts
+    // at k = 0 and N/2 dropped)
+    auto ld_in = [=](int idx, int b0, C* o) {
+      const bool up = 2 * idx > N;
+      const int k = up ? N - idx : idx;
       const bool self = (k == 0) || (2 * k == N);
-      const int r0 = 4 * q;
-      C x[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) x[i] = r0 + i < rows ? in[(r0 + i) * hs + k] : zero<C>();
-      C lo[2], hi[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        C xa = x[2 * h], xb = x[2 * h + 1];
+      for (int q = 0; q < V; ++q) {
+        const int ra = 2 * (b0 + q);
+        C xa = ra < rows ? in[c2r_in_row(ra, hs) + k] : zero<C>();
+        C xb = ra + 1 < rows ? in[c2r_in_row(ra + 1, hs) + k] : zero<C>();
         if (self) { xa.y = T(0); xb.y = T(0); }
-        lo[h] = mk<C>(xa.x - xb.y, xa.y + xb.x);
-        hi[h] = mk<C>(xa.x + xb.y, xb.x - xa.y);
+        o[q] = up ? mk<C>(xa.x + xb.y, xb.x - xa.y) : mk<C>(xa.x - xb.y, xa.y + xb.x);
       }
-      const int pk = ct::RowAt<C, TB, P::first_r>(k)(2 * q);
-      if (TF_IN(kSiteSmem + 3, pk + 1, N * TB)) Vec<2, C>::st(buf + pk, lo);
-      if (!self) {
-        const int pc = ct::RowAt<C, TB, P::first_r>(N - k)(2 * q);
-        if (TF_IN(kSiteSmem + 3, pc + 1, N * TB)) Vec<2, C>::st(buf + pc, hi);
-      }
-    });
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (t + gridDim.x < ntiles) {
-        bulk::fence_proxy_async();
-        issue(t + gridDim.x);
-      }
-      bulk::wait_read_all();
-    }
-    const ct::Buf<C, TB, V, P::first_r, TF_ROWS_PIPE_STEP> b{buf, N * TB};
-    P::template run<TB, V, NT, true, false, TF_ROWS_PIPE_STEP>(tw, buf, b, b);
+    };
     const T* scale = a.scale ? a.scale + (int64_t)tile * RT * L : nullptr;
-    visit_pairs<NT, TP>(L, [&](int i, int q) {
-      const int r0 = 4 * q;
-      if (r0 >= rows) return;
-      C z[2];
-      const int p = ct::RowAt<C, TB, P::first_r>(off + i)(2 * q);
-      if (TF_IN(kSiteSmem + 3, p + 1, N * TB)) Vec<2, C>::ld(buf + p, z);
-      const T y[4] = {z[0].x, z[0].y, z[1].x, z[1].y};
+    // last pass: the window [off, off + L) of each sequence's real and imaginary parts
+    // straight into the output tile
+    auto st_out = [=](int idx, int b0, const C* v, int) {
+      const int i = idx - off;
+      if (i < 0 || i >= L) return;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (r0 + j >= rows) break;
-        const int o = (r0 + j) * L + i;
-        out[o] = scale ? y[j] * scale[o] : y[j];
+      for (int q = 0; q < V; ++q) {
+        const int ra = 2 * (b0 + q);
+        if (ra < rows) out[ra * L + i] = scale ? v[q].x * scale[ra * L + i] : v[q].x;
+        if (ra + 1 < rows) out[(ra + 1) * L + i] = scale ? v[q].y * scale[(ra + 1) * L + i] : v[q].y;
       }
-    });
+    };
+    auto hook = [&]() {
+      if (threadIdx.x == 0) {
+        if (t + gridDim.x < ntiles) {
+          bulk::fence_proxy_async();
+          issue(t + gridDim.x);
+        }
+        bulk::wait_read_all();   // the previous tile's output has left `out`
+      }
+    };
+    P::template run_h<TB, V, NT, true, false, TF_ROWS_PIPE_STEP>(tw, buf, ld_in, st_out, hook);
     bulk::fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -973,7 +975,7 @@ cudaError_t rows_c2r_pipe(const RowsC2R<T>& a, int ncols, cudaStream_t s, bool* 
     return cudaSuccess;
   PipeDev d;
   if (pipe_dev(&d) != cudaSuccess) return cudaSuccess;
-  const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB + RT * a.hs) * sizeof(C) +
+  const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB + c2r_in_row(RT, a.hs)) * sizeof(C) +
                     (((size_t)RT * a.out_len * sizeof(T) + 15) & ~(size_t)15);
   RowsPipe pp{(a.nrows + RT - 1) / RT, ncols, d.status};
   const int64_t ntiles = (int64_t)pp.tiles_per_col * ncols;

@@ -289,10 +289,16 @@ template <int N, int Ns, int TwOff, int... Rs> struct Run;
 // Pass K of a plan stores into buffer slot (PP ? K mod 2 : 0) and loads from the slot
 // the previous pass stored into; with PP (two buffers, bufs[0] and bufs[1]) consecutive
 // passes alternate slots and need no barrier between their loads and stores.
+// A hook runs (in every thread) after the first pass's closing barrier, when the first
+// loader's source is no longer read.
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
 template <int N, int Ns, int TwOff, int R, int... Rest> struct Run<N, Ns, TwOff, R, Rest...> {
   template <int TB, int V, int NT, bool INV, bool FIRST, bool ZHI, int S, int STEP, bool PP, int K, typename C,
-            class L0, class SL>
-  static __device__ __forceinline__ void go(const C* tw, C* const* bufs, const L0& first, const SL& last) {
+            class L0, class SL, class H>
+  static __device__ __forceinline__ void go(const C* tw, C* const* bufs, const L0& first, const SL& last,
+                                            const H& hook) {
     constexpr bool LAST = sizeof...(Rest) == 0;
     constexpr int SO = PP ? K % 2 : 0, SI = PP ? (K + 1) % 2 : 0;
     const Buf<C, TB, V, S, STEP, SO> bo{bufs[SO], N * TB};
@@ -301,9 +307,10 @@ template <int N, int Ns, int TwOff, int R, int... Rest> struct Run<N, Ns, TwOff,
     else if constexpr (FIRST) pass<R, Ns, N, TB, V, NT, INV, ZHI>(tw + TwOff, first, bo);
     else if constexpr (LAST) pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, bi, last);
     else pass<R, Ns, N, TB, V, NT, INV>(tw + TwOff, bi, bo);
+    if constexpr (FIRST) hook();
     if constexpr (!LAST)
       Run<N, Ns * R, TwOff + Ns * (R - 1), Rest...>::template go<TB, V, NT, INV, false, false, S, STEP, PP,
-                                                                   K + 1>(tw, bufs, first, last);
+                                                                   K + 1>(tw, bufs, first, last, hook);
   }
 };
 
@@ -329,7 +336,14 @@ template <int N, int... Rs> struct Plan {
   static __device__ __forceinline__ void run(const C* tw, C* buf, const L0& first, const SL& last) {
     C* const bufs[2] = {buf, buf};
     Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r, STEP, false, 0>(
-        tw, bufs, first, last);
+        tw, bufs, first, last, NoHook{});
+  }
+  // run with a hook after the first pass
+  template <int TB, int V, int NT, bool INV, bool ZHI = false, int STEP = 0, typename C, class L0, class SL, class H>
+  static __device__ __forceinline__ void run_h(const C* tw, C* buf, const L0& first, const SL& last, const H& hook) {
+    C* const bufs[2] = {buf, buf};
+    Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r, STEP, false, 0>(
+        tw, bufs, first, last, hook);
   }
   // The same with two buffers: pass K stores into slot K mod 2 (a first loader that is a
   // Buf of slot 1 reads bufs[1]).
@@ -337,7 +351,7 @@ template <int N, int... Rs> struct Plan {
   static __device__ __forceinline__ void run2(const C* tw, C* buf0, C* buf1, const L0& first, const SL& last) {
     C* const bufs[2] = {buf0, buf1};
     Run<N, 1, 0, Rs...>::template go<TB, V, NT, INV, true, ZHI && can_zero_hi, first_r, STEP, true, 0>(
-        tw, bufs, first, last);
+        tw, bufs, first, last, NoHook{});
   }
 };
 
