@@ -32,6 +32,10 @@ LENGTHS = [
     ("r299_c349", synth.Grid(140, 170, 2, 10, 10, 5, 5), "magnetic", 35.0, -20.0),
     # rows 399, cols 499 (c4's two minimum lengths, swapped axes)
     ("r399_c499", synth.Grid(200, 250, 2), "gravity", 90.0, 0.0),
+    # rows 303 (n1 = 320) with an odd row length (nx = 153) and ragged row counts (303 model
+    # rows, 101 data rows): their last 16-row tiles are not whole 16-byte blocks, so the
+    # row stages take the per-tile kernels instead of the bulk-copy ones
+    ("r303_c201_odd", synth.Grid(151, 101, 3, 1, 1, 0, 0), "magnetic", 60.0, 5.0),
 ]
 
 _tables = {}
