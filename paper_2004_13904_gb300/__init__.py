@@ -76,9 +76,11 @@ class Operator:
 
     # -- plumbing -----------------------------------------------------------------------
     def close(self):
+        """Frees the operator; raises TFError when tf_destroy reports a fault of pending work
+        or a device-side wait that ran out (TF_ETIMEOUT)."""
         if getattr(self, "_h", None):
-            _lib.lib().tf_destroy(self._h)
-            self._h = None
+            h, self._h = self._h, None
+            _lib.check(_lib.lib().tf_destroy(h))
 
     def __del__(self):
         try:
