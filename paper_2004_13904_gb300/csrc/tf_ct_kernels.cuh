@@ -80,12 +80,20 @@ template <typename T> constexpr int kFwdThreadsPerSM = 512;
 // 320, 448 and 512 resident threads per SM)
 constexpr int kWideThreadsPerSM = 384;
 // the adjoint at n >= 448 (256 threads per CTA) measured fastest with a tighter budget
-template <typename T, int N> constexpr int kAdjThreadsPerSM = N >= 448 ? 768 : 640;
-// Buffer positions from per-task bases (Buf's STEP) in the forward column kernel only: c4
-// cols_fwd 14.99 -> 13.71 ms per 2510-column step, while the adjoint measured slower with
-// them for its loads (14.56 -> 16.3 ms at its 80-register budget, 16.0 ms at 128
-// registers) and no faster for its stores alone.
-constexpr int kAdjStep = 0;
+#ifndef TF_ADJ_TPSM
+#define TF_ADJ_TPSM 768
+#endif
+template <typename T, int N> constexpr int kAdjThreadsPerSM = N >= 448 ? TF_ADJ_TPSM : 640;
+// Buffer positions from per-task bases (Buf's STEP): c4 cols_fwd 14.99 -> 13.71 ms per
+// 2510-column step.  The adjoint with single-buffer passes measured slower with them
+// (14.56 -> 16.3 ms at its 80-register budget, 16.0 ms at 128 registers).
+// With the data spectrum in TMEM and two-buffer passes, the adjoint's single-precision
+// 256-thread plans take per-task bases after all (c4: cols_adj 12.57 -> 12.41 ms at 80
+// registers).
+#ifndef TF_ADJ_STEP
+#define TF_ADJ_STEP 3
+#endif
+template <typename T, int NT> constexpr int kAdjStepOf = std::is_same<T, float>::value && NT == 256 ? TF_ADJ_STEP : 0;
 // The row kernels keep per-element positions too (with bases: rows_r2c 7.96 -> 8.8 ms, and
 // at a 48-register budget 8.9 ms; rows_c2r 8.41 -> 8.62 ms).
 constexpr int kRowsStep = 0;
@@ -795,7 +803,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
     if (TF_IN(kSiteSmem + 2, idx * TB + b0 + V - 1, N * TB)) Vec<V, C>::st(dsp + idx * TB + b0, v);
   };
   if constexpr (kTm) {
-    P::template run2<TB, V, NT, false, false, kAdjStep>(tw, buf, acc, load, sacc);
+    P::template run2<TB, V, NT, false, false, kAdjStepOf<T, NT>>(tw, buf, acc, load, sacc);
     // slot r of a thread: input r of its first-pass task (element j + r NB0 of pair b0)
     if (threadIdx.x < AT::TOTAL0) {
       const int j = threadIdx.x / (TB / V), b0 = (threadIdx.x % (TB / V)) * V;
@@ -811,7 +819,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
     tmem::wait_st();
     __syncthreads();
   } else {
-    P::template run<TB, V, NT, false, false, kAdjStep>(tw, buf, load, sacc);
+    P::template run<TB, V, NT, false, false, kAdjStepOf<T, NT>>(tw, buf, load, sacc);
   }
   C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
   const C* spec = a.spec;
@@ -834,9 +842,9 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
     };
     if constexpr (kTm) {
       const AdjSpecTask<C, V> pt{tspec, spec, goff, hs, k0, nh, g_ext};
-      P::template run2<TB, V, NT, true, false, kAdjStep>(tw, buf, acc, pt, store);
+      P::template run2<TB, V, NT, true, false, kAdjStepOf<T, NT>>(tw, buf, acc, pt, store);
     } else {
-      P::template run<TB, V, NT, true, false, kAdjStep>(tw, buf, prod, store);
+      P::template run<TB, V, NT, true, false, kAdjStepOf<T, NT>>(tw, buf, prod, store);
     }
   }
   if constexpr (kTm) {
