@@ -67,6 +67,35 @@ __device__ __forceinline__ void load_tile_2d(void* dst, const void* tmap, int x,
       "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(saddr(bar))
       : "memory");
 }
+// The same with an L2 eviction policy for the copied lines (policy_*)
+__device__ __forceinline__ void load_tile_2d_hint(void* dst, const void* tmap, int x, int y, uint64_t* bar,
+                                                  uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+      "%3}], [%4], %5;" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(saddr(bar)), "l"(pol)
+      : "memory");
+}
+// L2 eviction policies for cache-hinted accesses: data read again soon (kept) and data
+// streamed through once (evicted first)
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// 16-byte global load with an L2 policy
+__device__ __forceinline__ float4 ld_hint(const void* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
 // shared -> global, in the thread's current bulk group
 __device__ __forceinline__ void store(void* dst, const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(saddr(src)),

@@ -66,6 +66,31 @@ __device__ __forceinline__ void ld_row_vec(const C* p, int k1, int nh, bool ok, 
   }
 }
 
+// Loads of the layer spectra, which every column of a block reads again, with an L2
+// evict-last policy (pol) in single precision; the row-transformed tiles that stream
+// through once are copied with evict-first.
+#ifndef TF_L2_HINTS
+#define TF_L2_HINTS 1
+#endif
+template <int V, typename C>
+__device__ __forceinline__ void ld_spec_vec(const C* p, int k1, int nh, bool ok, C* o, uint64_t pol) {
+  if constexpr (TF_L2_HINTS && V == 2 && std::is_same<C, float2>::value) {
+    if (ok) {
+      const float4 t = bulk::ld_hint(p, pol);
+      o[0] = make_float2(t.x, t.y);
+      o[1] = make_float2(t.z, t.w);
+    } else {
+      o[0] = o[1] = zero<C>();
+    }
+  } else {
+    ld_row_vec<V, false>(p, k1, nh, ok, o);
+  }
+}
+template <typename C> __device__ __forceinline__ uint64_t spec_policy() {
+  if constexpr (TF_L2_HINTS && std::is_same<C, float2>::value) return bulk::policy_evict_last();
+  else return 0;
+}
+
 // Register budgets of the column kernels, as a minimum number of resident CTAs per SM
 // for __launch_bounds__ (measured with 1260-column blocks at transform lengths 64 to
 // 512: the single-precision forward kernel is fastest near 128 registers a thread, the
@@ -573,11 +598,16 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   const int z_ext = a.nz * ny * hs, g_ext = a.nz * N * hs, s_ext = sy * hs;
   const C* spec = a.spec;
   const int zrows = (int)(a.z_ld / hs);   // workspace rows per model column
+  const uint64_t spol = spec_policy<C>();
+  const uint64_t zpol = TF_L2_HINTS && kTile ? bulk::policy_evict_first() : 0;
   auto issue = [&](int c, int r) {
     if (threadIdx.x == 0) {
       bulk::fence_proxy_async();
       bulk::mbar_expect_tx(&zbar[c], (uint32_t)(ny * TB * sizeof(C)));
-      bulk::load_tile_2d(ztile + c * ny * TB, &zmap, 2 * k0, (col0 + c) * zrows + r * ny, &zbar[c]);
+      if constexpr (TF_L2_HINTS)
+        bulk::load_tile_2d_hint(ztile + c * ny * TB, &zmap, 2 * k0, (col0 + c) * zrows + r * ny, &zbar[c], zpol);
+      else
+        bulk::load_tile_2d(ztile + c * ny * TB, &zmap, 2 * k0, (col0 + c) * zrows + r * ny, &zbar[c]);
     }
   };
   if constexpr (kTile)
@@ -594,8 +624,8 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
 #pragma unroll
       for (int rr = 0; rr < RL; ++rr) {
         const int e = goff + (base + rr * NSL) * hs + k1;
-        ld_row_vec<V, false>(spec + e, k1, nh, u < LM::TOTAL && k1 < nh && TF_IN(kSiteFwdSpec, e + V - 1, g_ext),
-                             gpre[it * RL + rr]);
+        ld_spec_vec<V>(spec + e, k1, nh, u < LM::TOTAL && k1 < nh && TF_IN(kSiteFwdSpec, e + V - 1, g_ext),
+                       gpre[it * RL + rr], spol);
       }
     }
     const bool first_layer = (r == 0);
@@ -742,6 +772,7 @@ template <typename C, int V> struct AdjSpecTask {
   uint32_t tspec;
   const C* spec;
   int goff, hs, k0, nh, g_ext;
+  uint64_t pol;
   template <int R, int NB> __device__ __forceinline__ void task(int j, int b0, C (&v)[V][R]) const {
     static_assert(V == 2 && R == 8, "32 TMEM columns per task");
     const int k1 = k0 + b0;
@@ -749,7 +780,7 @@ template <typename C, int V> struct AdjSpecTask {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int e = goff + (j + r * NB) * hs + k1;
-      ld_row_vec<V, false>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteAdjSpec, e + V - 1, g_ext), gv[r]);
+      ld_spec_vec<V>(spec + e, k1, nh, k1 < nh && TF_IN(kSiteAdjSpec, e + V - 1, g_ext), gv[r], pol);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -823,6 +854,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   }
   C* u = a.u + (int64_t)blockIdx.y * a.u_ld;
   const C* spec = a.spec;
+  const uint64_t spol = spec_policy<C>();
   for (int r = 0; r < a.nz; ++r) {
     const int goff = r * N * hs, uoff = r * ny * hs;
     auto prod = [=](int idx, int b0, C* o) {
@@ -841,7 +873,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
       if (TF_IN(kSiteAdjU, e + V - 1, u_ext)) Vec<V, C>::st(u + e, v);
     };
     if constexpr (kTm) {
-      const AdjSpecTask<C, V> pt{tspec, spec, goff, hs, k0, nh, g_ext};
+      const AdjSpecTask<C, V> pt{tspec, spec, goff, hs, k0, nh, g_ext, spol};
       P::template run2<TB, V, NT, true, false, kAdjStepOf<T, NT>>(tw, buf, acc, pt, store);
     } else {
       P::template run<TB, V, NT, true, false, kAdjStepOf<T, NT>>(tw, buf, prod, store);
