@@ -304,7 +304,7 @@ struct RowsPipe {
 #endif
 
 template <typename T, class P, int TB, int V, int NT, bool ZHI>
-__global__ void __launch_bounds__(NT, 2) k_rows_r2c_pipe(const RowsR2C<T> a, const RowsPipe pp) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_rows_r2c_pipe(const RowsR2C<T> a, const RowsPipe pp) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n, NH = N / 2 + 1, TP = TB / 2, RT = 2 * TB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -403,12 +403,13 @@ __global__ void __launch_bounds__(NT, 2) k_rows_r2c_pipe(const RowsR2C<T> a, con
   if (threadIdx.x == 0) bulk::wait_all();
 }
 
-// Rows of the c2r input tile sit at row * hs + 4 (row / 4) values: the first pass's loads
-// of rows 0, 4, 8, 12 (one per sequence pair of a half-warp) then fall in different banks.
-__host__ __device__ constexpr int c2r_in_row(int r, int hs) { return r * hs + 4 * (r >> 2); }
+// Rows of the c2r input tile (RT rows) sit at row * hs + (64 / RT) (row / 4) values: the
+// first pass's loads of rows 0, 4, ... (one per sequence pair of a half-warp) then fall in
+// different banks.
+template <int RT> __host__ __device__ constexpr int c2r_in_row(int r, int hs) { return r * hs + (64 / RT) * (r >> 2); }
 
 template <typename T, class P, int TB, int V, int NT>
-__global__ void __launch_bounds__(NT, 2) k_rows_c2r_pipe(const RowsC2R<T> a, const RowsPipe pp) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_rows_c2r_pipe(const RowsC2R<T> a, const RowsPipe pp) {
   typedef typename CT<T>::C C;
   constexpr int N = P::n, RT = 2 * TB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(NT, 2) k_rows_c2r_pipe(const RowsC2R<T> a, con
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + twpad(N - 1);
   C* in = buf + N * TB;                                   // rows at c2r_in_row
-  T* out = reinterpret_cast<T*>(in + c2r_in_row(RT, hs));  // [RT][L], the global layout
+  T* out = reinterpret_cast<T*>(in + c2r_in_row<RT>(RT, hs));  // [RT][L], the global layout
   const int64_t ntiles = (int64_t)tpc * pp.ncols;
   auto issue = [&](int64_t t) {
     const int col = (int)(t / tpc), tile = (int)(t - (int64_t)col * tpc);
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(NT, 2) k_rows_c2r_pipe(const RowsC2R<T> a, con
     const C* src = a.src + (int64_t)col * a.src_ld + (int64_t)tile * RT * hs;
     bulk::mbar_expect_tx(&bar, (uint32_t)(rows * hs * sizeof(C)));
     for (int r = 0; r < rows; ++r)
-      bulk::load(in + c2r_in_row(r, hs), src + (int64_t)r * hs, (uint32_t)(hs * sizeof(C)), &bar);
+      bulk::load(in + c2r_in_row<RT>(r, hs), src + (int64_t)r * hs, (uint32_t)(hs * sizeof(C)), &bar);
   };
   if (threadIdx.x == 0) {
     bulk::mbar_init(&bar, 1);
@@ -457,8 +458,8 @@ __global__ void __launch_bounds__(NT, 2) k_rows_c2r_pipe(const RowsC2R<T> a, con
 #pragma unroll
       for (int q = 0; q < V; ++q) {
         const int ra = 2 * (b0 + q);
-        C xa = ra < rows ? in[c2r_in_row(ra, hs) + k] : zero<C>();
-        C xb = ra + 1 < rows ? in[c2r_in_row(ra + 1, hs) + k] : zero<C>();
+        C xa = ra < rows ? in[c2r_in_row<RT>(ra, hs) + k] : zero<C>();
+        C xb = ra + 1 < rows ? in[c2r_in_row<RT>(ra + 1, hs) + k] : zero<C>();
         if (self) { xa.y = T(0); xb.y = T(0); }
         o[q] = up ? mk<C>(xa.x + xb.y, xb.x - xa.y) : mk<C>(xa.x - xb.y, xa.y + xb.x);
       }
@@ -978,9 +979,16 @@ inline cudaError_t pipe_dev(PipeDev* out) {
   return cudaSuccess;
 }
 
+// Tiles of the bulk-copy row kernels: TB sequences (2 TB rows) per CTA.
+#ifndef TF_PIPE_TB
+#define TF_PIPE_TB 4
+#endif
+struct PipeTiles {
+  static constexpr int TB = TF_PIPE_TB, V = 2, NT = 32 * TB, PER_SM = 16 / TB;
+};
 template <typename T, class P>
 cudaError_t rows_r2c_pipe(const RowsR2C<T>& a, int ncols, cudaStream_t s, bool* used) {
-  typedef Tiles<T, P::n> TL;
+  typedef PipeTiles TL;
   constexpr int RT = 2 * TL::TB;
   typedef typename CT<T>::C C;
   *used = false;
@@ -993,7 +1001,7 @@ cudaError_t rows_r2c_pipe(const RowsR2C<T>& a, int ncols, cudaStream_t s, bool* 
   const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB + RT * a.hs) * sizeof(C) + in_bytes;
   RowsPipe pp{(a.nrows + RT - 1) / RT, ncols, d.status};
   const int64_t ntiles = (int64_t)pp.tiles_per_col * ncols;
-  const int grid = (int)std::min<int64_t>(ntiles, 2 * (int64_t)d.sms);
+  const int grid = (int)std::min<int64_t>(ntiles, TL::PER_SM * (int64_t)d.sms);
   if (grid <= 0) return cudaSuccess;
   *used = true;
   const bool zhi = P::can_zero_hi && a.seq_off >= 0 && a.seq_off + a.row_len <= P::n / 2;
@@ -1011,7 +1019,7 @@ cudaError_t rows_r2c_pipe(const RowsR2C<T>& a, int ncols, cudaStream_t s, bool* 
 }
 template <typename T, class P>
 cudaError_t rows_c2r_pipe(const RowsC2R<T>& a, int ncols, cudaStream_t s, bool* used) {
-  typedef Tiles<T, P::n> TL;
+  typedef PipeTiles TL;
   constexpr int RT = 2 * TL::TB;
   typedef typename CT<T>::C C;
   *used = false;
@@ -1020,11 +1028,11 @@ cudaError_t rows_c2r_pipe(const RowsC2R<T>& a, int ncols, cudaStream_t s, bool* 
     return cudaSuccess;
   PipeDev d;
   if (pipe_dev(&d) != cudaSuccess) return cudaSuccess;
-  const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB + c2r_in_row(RT, a.hs)) * sizeof(C) +
+  const size_t sm = (size_t)(twpad(P::n - 1) + P::n * TL::TB + c2r_in_row<RT>(RT, a.hs)) * sizeof(C) +
                     (((size_t)RT * a.out_len * sizeof(T) + 15) & ~(size_t)15);
   RowsPipe pp{(a.nrows + RT - 1) / RT, ncols, d.status};
   const int64_t ntiles = (int64_t)pp.tiles_per_col * ncols;
-  const int grid = (int)std::min<int64_t>(ntiles, 2 * (int64_t)d.sms);
+  const int grid = (int)std::min<int64_t>(ntiles, TL::PER_SM * (int64_t)d.sms);
   if (grid <= 0) return cudaSuccess;
   *used = true;
   constexpr auto k = k_rows_c2r_pipe<T, P, TL::TB, TL::V, TL::NT>;

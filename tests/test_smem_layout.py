@@ -164,3 +164,65 @@ def test_forward_accumulator_tmem_budget():
         assert min(233472 // (max((tw + 2 * N * TB) * 8, floor) + 1024), 2048 // NT) * 128 <= 512
         used += 1
     assert used >= 3          # 320, 448 and 512
+
+
+def _pipe_tb():
+    text = open(HDR).read()
+    return int(re.search(r"#define TF_PIPE_TB (\d+)", text).group(1))
+
+
+@pytest.mark.parametrize("N,radices", [(e[0], e[1:]) for e in _menu("TF_CT_MENU") if e[0] > 256])
+def test_bulk_copy_row_tiles_are_bank_conflict_free(N, radices):
+    """The bulk-copy row kernels (lengths above 256) run TF_PIPE_TB sequences on 32 TB
+    threads: the position map stays a bijection and every pass moves its 16-byte slots at
+    the minimum number of wavefronts.  The first pass of rows_c2r reads each sequence pair's
+    rows 2b, 2b + 1 from the copied input tile, whose row r starts at r hs + (64 / RT)(r / 4)
+    values (RT = 2 TB rows): its 8-byte loads also need the minimum (two per warp)."""
+    TB, V = _pipe_tb(), 2
+    NT, RT = 32 * TB, 2 * TB
+    at = _at(TB, 8, radices[0])
+    assert sorted(at(i, b) for i in range(N) for b in range(TB)) == list(range(N * TB))
+    G = TB // V
+    Ns = 1
+    for R in radices:
+        NB = N // R
+        total = NB * G
+        for w in range(NT // 32):
+            for it in range((total + NT - 1) // NT):
+                us = [w * 32 + lane + it * NT for lane in range(32)]
+                active = sum(u < total for u in us)
+                if not active:
+                    continue
+                for r in range(R):
+                    loads, stores = [], []
+                    for u in us:
+                        if u >= total:
+                            loads.append(None)
+                            stores.append(None)
+                            continue
+                        j, b0 = u // G, (u % G) * V
+                        k = j % Ns
+                        loads.append(2 * at(j + r * NB, b0))
+                        stores.append(2 * at((j - k) * R + k + r * Ns, b0))
+                    minimum = (active * 16 + 127) // 128
+                    assert _wavefronts(loads, 16) == minimum, (N, radices, R, "load")
+                    assert _wavefronts(stores, 16) == minimum, (N, radices, R, "store")
+        Ns *= R
+    hs = ((N // 2 + 1) + 15) // 16 * 16
+    in_row = lambda r: r * hs + (64 // RT) * (r // 4)
+    R = radices[0]
+    NB = N // R
+    for w in range((NB * G + 31) // 32):
+        us = [w * 32 + lane for lane in range(32) if w * 32 + lane < NB * G]
+        for r in range(R):
+            for q in range(V):
+                for half in range(2):            # row 2b and row 2b + 1
+                    addrs = []
+                    for u in us:
+                        j, b0 = u // G, (u % G) * V
+                        idx = j + r * NB
+                        k = N - idx if 2 * idx > N else idx
+                        addrs.append(2 * (in_row(2 * (b0 + q) + half) + k))
+                    addrs += [None] * (32 - len(addrs))
+                    minimum = (len(us) * 8 + 127) // 128
+                    assert _wavefronts(addrs, 8) == minimum, (N, radices, r, q, half)
