@@ -149,9 +149,11 @@ tf_status tf_get_spectra(const tf_op* op, void* dst, int64_t bytes, tf_stream st
  * plans have fixed tiles), and columns per workspace chunk (>= 1; the workspace is
  * reallocated to exactly that many columns and no longer grows).  0 keeps the current
  * value.  By default the workspace grows, on the first product with more columns than
- * it holds, up to the columns that fit in 2 GiB (the growth frees and allocates device
- * memory, which waits for the device to be idle).  Must not be called while products of
- * this operator are in flight. */
+ * it holds, up to the columns that fit in 16 GiB, or in an eighth of the device memory
+ * free when the operator was created if that is less (the growth frees and allocates
+ * device memory, which waits for the device to be idle); a block is processed in the
+ * fewest chunks of equal size.  Must not be called while products of this operator are
+ * in flight. */
 tf_status tf_set_tuning(tf_op* op, int rows_tile, int cols_tile, int64_t chunk_cols);
 tf_status tf_get_tuning(const tf_op* op, int* rows_tile, int* cols_tile, int64_t* chunk_cols);
 

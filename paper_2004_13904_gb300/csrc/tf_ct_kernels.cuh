@@ -523,6 +523,12 @@ template <typename T> constexpr bool kSpecPrefetch = std::is_same<T, float>::val
 #ifndef TF_FWD_PP
 #define TF_FWD_PP 1   // measured: c4 cols_fwd 13.72 -> 12.66 ms per step with the two buffers
 #endif
+// Values between consecutive model columns' layer tiles ([ny][TB] each) in cols_fwd's
+// shared memory: the tile rounded up to 128 bytes, the alignment of a tensor copy's
+// shared-memory destination.
+template <typename C, int TB> __host__ __device__ constexpr int fwd_tile_stride(int ny) {
+  return (int)(((size_t)ny * TB * sizeof(C) + 127) / 128 * 128 / sizeof(C));
+}
 template <typename T, class P, int TB, int V, int NT> struct FwdTmem {
   typedef ct::PassMap<P::last_r, P::last_ns, P::n, TB, V> LM;
   static constexpr int ITA = (LM::TOTAL + NT - 1) / NT;
@@ -569,6 +575,8 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
   C* acc = buf + N * TB;
   // [MC][ny][TB] with TILE, 128-byte aligned (the launch adds 128 bytes)
   C* ztile = reinterpret_cast<C*>((reinterpret_cast<uintptr_t>(acc + N * TB) + 127) & ~(uintptr_t)127);
+  // a tensor copy writes shared memory at 128-byte boundaries: each column's tile starts on one
+  const int zstride = fwd_tile_stride<C, TB>(a.ny);
   if constexpr (kTm)
     if (threadIdx.x < 32) tmem::alloc(&tm_base, FT::kCols);
   if constexpr (kTile)
@@ -606,9 +614,9 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
       bulk::fence_proxy_async();
       bulk::mbar_expect_tx(&zbar[c], (uint32_t)(ny * TB * sizeof(C)));
       if constexpr (TF_L2_HINTS)
-        bulk::load_tile_2d_hint(ztile + c * ny * TB, &zmap, 2 * k0, (col0 + c) * zrows + r * ny, &zbar[c], zpol);
+        bulk::load_tile_2d_hint(ztile + c * zstride, &zmap, 2 * k0, (col0 + c) * zrows + r * ny, &zbar[c], zpol);
       else
-        bulk::load_tile_2d(ztile + c * ny * TB, &zmap, 2 * k0, (col0 + c) * zrows + r * ny, &zbar[c]);
+        bulk::load_tile_2d(ztile + c * zstride, &zmap, 2 * k0, (col0 + c) * zrows + r * ny, &zbar[c]);
     }
   };
   if constexpr (kTile)
@@ -651,7 +659,7 @@ __global__ void __launch_bounds__(NT, cols_min_blocks<T>(NT, P::first_r >= 16 ? 
           return;
         }
       }
-      const C* zt = ztile + c * ny * TB;
+      const C* zt = ztile + c * zstride;
       auto load = [=](int idx, int b0, C* o) {
         if constexpr (kTile) {
           if (idx < ny && TF_IN(kSiteSmem + 4, idx * TB + b0 + V - 1, ny * TB)) {
@@ -1127,7 +1135,7 @@ cudaError_t cols_fwd(const ColsFwd<T>& a, int ncols, cudaStream_t s) {
     // tensor-copied layer tiles: a box of TB values by ny rows, and room for the tiles
     // within the two CTAs per SM that the register budget allows
     typedef typename CT<T>::C C;
-    const size_t st = sm + 128 + (size_t)FT::MC * a.ny * TL::TB * sizeof(C);
+    const size_t st = sm + 128 + (size_t)FT::MC * fwd_tile_stride<C, TL::TB>(a.ny) * sizeof(C);
     if (st <= kFwdTileSmemMax && encode_rows_map(a.z, a.z_ld, a.hs, a.ny, ncols, TL::TB, &zmap)) {
       if (zhi) return launch_fwd<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, true, true>>(ac, zmap, grid, TL::NT, st, s);
       return launch_fwd<k_cols_fwd<T, P, TL::TB, TL::V, TL::NT, false, true>>(ac, zmap, grid, TL::NT, st, s);

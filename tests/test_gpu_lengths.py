@@ -36,6 +36,11 @@ LENGTHS = [
     # rows, 101 data rows): their last 16-row tiles are not whole 16-byte blocks, so the
     # row stages take the per-tile kernels instead of the bulk-copy ones
     ("r303_c201_odd", synth.Grid(151, 101, 3, 1, 1, 0, 0), "magnetic", 60.0, 5.0),
+    # cols 257 (n2 = 320) with an odd layer row count (ny = 139): the forward column
+    # kernel's second model column's layer tile must still start on a 128-byte boundary
+    ("r79_c257_oddny", synth.Grid(37, 119, 3, 3, 3, 10, 10), "magnetic", 45.0, 10.0),
+    # rows 261 (n1 = 320) with odd ny (117) and 351 model rows (a 7-row last tile)
+    ("r261_c225_oddny", synth.Grid(126, 109, 3, 5, 5, 4, 4), "gravity", 90.0, 0.0),
 ]
 
 _tables = {}
