@@ -54,11 +54,11 @@ METRIC = "G/G^T column products per second"
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the hash of
 # the kernel sources at capture time (null once the kernels change): the bytes of one
 # captured launch scaled to the benchmark's launch by its columns.
-# c4, FP32, one 64-column launch each: cols_fwd 674.6 MB (DRAM read 650.1 + write 24.5), cols_adj 581.9 MB
-# (read 101.8 + write 480.1).
+# c4, FP32, one 64-column launch each: cols_fwd 590.9 MB (DRAM read 583.5 + write 7.4), cols_adj 535.6 MB
+# (read 55.0 + write 480.6).
 NCU_TRAFFIC = {
-    ("cols_fwd", "c4", "f32"): {"hash": "6d07e79e77652a0a", "bytes_per_launch": 674.6e6, "columns": 64},
-    ("cols_adj", "c4", "f32"): {"hash": "6d07e79e77652a0a", "bytes_per_launch": 581.9e6, "columns": 64},
+    ("cols_fwd", "c4", "f32"): {"hash": "10ad239315c6801e", "bytes_per_launch": 590.9e6, "columns": 64},
+    ("cols_adj", "c4", "f32"): {"hash": "10ad239315c6801e", "bytes_per_launch": 535.6e6, "columns": 64},
 }
 
 
