@@ -275,15 +275,15 @@ __global__ void __launch_bounds__(NT, rows_min_blocks<T>(NT, 1280)) k_rows_c2r(c
   });
 }
 
-// Persistent row kernels with bulk copies (single precision).  A tile is the 2 TB real rows
-// that the plain row kernels give one CTA; its rows are consecutive in memory, so the
-// input is one contiguous block and so is the output.  Each CTA walks the tiles of all
-// columns (stride gridDim.x).  One thread moves a tile's input into shared memory with one
-// bulk copy, issued as soon as the previous tile is staged, so it lands while the CTA
-// transforms; the unpacked output goes to a shared-memory tile in the global layout and
-// leaves with one bulk store that completes while the CTA works on the next tile.  DRAM
-// latency is hidden by the copies in flight instead of by resident warps, so the kernels
-// run two CTAs per SM with the register budget that needs.
+// Persistent row kernels with bulk copies (single precision).  A tile is 2 TB consecutive
+// real rows (TB two-row sequences, PipeTiles), so its input is one contiguous block and so
+// is its output.  Each CTA walks the tiles of all columns (stride gridDim.x).  One thread
+// moves a tile's input into shared memory with bulk copies, issued right after the previous
+// tile's first FFT pass has read its input, so it lands while the CTA transforms; the first
+// pass reads the copied rows directly, and the output goes to a shared-memory tile in the
+// global layout that leaves with one bulk store, which completes while the CTA works on the
+// next tile.  DRAM latency is hidden by the copies in flight instead of by resident warps,
+// so the kernels run few CTAs per SM (PipeTiles::PER_SM) with the registers that allows.
 // The output tile of rows_r2c includes each row's padding [nh, hs), zeroed once, so the
 // workspace's padding stays zero.  Every wait on the input barrier is bounded: past
 // kPipeWaitNs the CTA records TF_ETIMEOUT in the status word and returns.
