@@ -50,7 +50,8 @@ typedef enum {
   TF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed               */
   TF_EUNSUPPORTED = 4,  /* valid but outside what the library supports (FFT size)   */
   TF_ENOTCONV = 5,      /* reserved for iterative drivers                            */
-  TF_ETIMEOUT = 6       /* a bounded device-side wait ran out (tf_batch_persistent)   */
+  TF_ETIMEOUT = 6       /* a bounded device-side wait ran out (tf_batch_persistent;  */
+                        /* the product kernels' copy waits, reported by tf_destroy)  */
 } tf_status;
 
 typedef enum { TF_F32 = 0, TF_F64 = 1 } tf_dtype;
@@ -85,7 +86,9 @@ tf_status tf_create_magnetic(const tf_grid* grid, double inc_deg, double dec_deg
                              double field_nt, tf_dtype dtype, tf_stream stream, tf_op** out);
 
 /* Release the operator and everything it owns (waits for the device's work to finish).
- * NULL is accepted.  Returns TF_ECUDA if that wait reports a fault of earlier work; the
+ * NULL is accepted.  Returns TF_ECUDA if that wait reports a fault of earlier work, and
+ * TF_ETIMEOUT if a product kernel's bounded wait for one of its asynchronous copies ran
+ * out (about 2 s; that kernel's outputs are then incomplete; the record is cleared); the
  * operator is released either way. */
 tf_status tf_destroy(tf_op* op);
 
