@@ -307,15 +307,15 @@ tf_status upload_twiddles(const HostPlan& h, tf_dtype dt, void** dst) {
 // Each workspace buffer carries a guard tail of one full transform column block
 // (n2 * hs complex values) beyond the last column it serves, so that no read near the
 // end of a column block can leave the allocation.
-tf_status alloc_workspace(tf_op* op, int64_t chunk) {
+tf_status alloc_workspace(tf_op* op, int64_t chunk, cudaError_t* err = nullptr) {
   cudaFree(op->w1);
   cudaFree(op->w2);
   op->w1 = op->w2 = nullptr;
   op->chunk = 0;
   const size_t guard = (size_t)op->n2 * op->hs * op->csize();
   cudaError_t e = cudaMalloc(&op->w1, (size_t)chunk * op->w1_per_col() * op->csize() + guard);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
-  e = cudaMalloc(&op->w2, (size_t)chunk * op->w2_per_col() * op->csize() + guard);
+  if (e == cudaSuccess) e = cudaMalloc(&op->w2, (size_t)chunk * op->w2_per_col() * op->csize() + guard);
+  if (err) *err = e;
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
   // zero once: the row padding (values nh..hs-1) is never written by the row kernels
   e = cudaMemset(op->w1, 0, (size_t)chunk * op->w1_per_col() * op->csize() + guard);
@@ -345,17 +345,28 @@ int64_t default_chunk_cap(const tf_op* op) {
 // Columns per chunk for a block of B columns with room for `chunk`: the fewest chunks, of
 // equal size (no short last chunk, whose launches would fill a fraction of the GPU).
 int64_t balanced_chunk(int64_t B, int64_t chunk) {
-  if (chunk <= 0 || B <= chunk) return std::max<int64_t>(B, 1);
+  if (B <= 0) return 0;
+  if (chunk <= 0 || B <= chunk) return B;
   const int64_t n = (B + chunk - 1) / chunk;
   return (B + n - 1) / n;
 }
 
 // Grows the workspace (once, stream-ordered through cudaFree's implicit
 // synchronisation) so that a block of B columns runs in as few chunks as the cap allows.
+// When the device cannot hold that many columns (other operators, the caller's buffers),
+// the product still runs in more, smaller chunks: the request halves until it fits, and
+// the smaller size becomes the operator's cap.
 tf_status ensure_workspace(tf_op* op, int64_t B) {
-  const int64_t want = balanced_chunk(B, op->chunk_cap);
+  int64_t want = balanced_chunk(B, op->chunk_cap);
   if (op->chunk >= want) return TF_OK;
-  return alloc_workspace(op, want);
+  for (;;) {
+    cudaError_t e = cudaSuccess;
+    const tf_status st = alloc_workspace(op, want, &e);
+    if (st == TF_OK || e != cudaErrorMemoryAllocation || want <= 1) return st;
+    cudaGetLastError();   // the failed allocation's (non-sticky) error
+    want = (want + 1) / 2;
+    op->chunk_cap = want;
+  }
 }
 
 tf_status create_common(const tf_grid* g, int kind, double inc, double dec, double field,
