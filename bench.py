@@ -291,7 +291,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline (no FP64/c2/error/CPU legs): for profiling runs")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--e2e-chunks", type=int, default=8,
                     help="column chunks of the host-buffer call (tf_products_host)")
     ap.add_argument("--columns", type=int, default=0,
